@@ -1,0 +1,346 @@
+/*
+ * d3_oracle.c -- plain FP64 CPU oracle for the D3(BJ) "two-body" dispersion
+ * correction of Ying & Fan, "Combining the D3 dispersion correction with the
+ * neuroevolution machine-learned potential" (arXiv 2310.05279), Sec. II A,
+ * Eqs. 1-7.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, obviously-correct
+ * reference that the CUDA library is checked against.  Only the tests, the
+ * package smoke check and the benchmark's CPU-baseline leg load it.  It shares
+ * no code, header, table or constant generator with the CUDA library.
+ *
+ * What it computes, in the paper's order, for one periodic (or open) structure:
+ *
+ *   1. every ordered pair instance (i, j, T): atom j shifted by the lattice
+ *      translation T, distance r = |x_j + T - x_i| in bohr, excluding only
+ *      (i, i, 0).  An atom's own periodic images are neighbours (Eqs. 2 and 4
+ *      sum over "j != i", read as "every instance but the atom itself").
+ *   2. Eq. 4: n_i = sum over instances with r < R_cn of
+ *             1 / (1 + exp(-k1 * (k2 * (Rcov_i + Rcov_j) / r - 1)))
+ *      (effective covalent radius = k2 * tabulated radius).
+ *   3. Eq. 3: C6_ij(n_i, n_j) = sum_ab C6ref_ab L_ia L_jb / sum_ab L_ia L_jb with
+ *      L_ia = exp(-k3 (n_i - nref_ia)^2).  The exponent is a sum of an i part and
+ *      a j part, so the ratio equals sum_ab W_ia W_jb C6ref_ab with per-atom
+ *      normalised weights W_ia = L_ia / sum_c L_ic.  Each atom's exponents are
+ *      shifted by their maximum before exponentiating; this leaves Eq. 3
+ *      unchanged wherever it is defined and gives its limit (all weight on the
+ *      nearest reference) where every L_ia underflows.
+ *   4. Eq. 2: E = -1/2 sum over ordered instances with r < R_pot of
+ *             s6 C6 / (r^6 + R^6) + s8 C8 / (r^8 + R^8),
+ *      R = a1 R0 + a2, R0^2 = 3 sqrtQ_i sqrtQ_j, C8 = C6 R0^2.
+ *   5. Forces F = -dE/dx by the chain rule through r directly and through the
+ *      coordination numbers (the dependence of U_i on n_j that makes D3
+ *      many-body, Sec. II A after Eq. 4).
+ *   6. Virial W = -sum over instances d (x) dE/dd, the sum of the per-atom
+ *      virials of Eq. 7.
+ *
+ * Units: positions and cells in Angstrom; a2, Rcov, sqrt(Q) in bohr; C6ref in
+ * Ha*bohr^6; all formulae evaluated in bohr/Hartree; E in eV, F in eV/A, W in eV.
+ * Cutoffs are hard: a term is included when r < cutoff.
+ *
+ * Every accumulation below is a plain loop in a fixed order; the only
+ * parallel part is the instance search (OpenMP over i, each thread writing
+ * its own rows), so results are deterministic.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORACLE_BOHR_A 0.529177210903      /* Angstrom per bohr (CODATA 2018) */
+#define ORACLE_HARTREE_EV 27.211386245988 /* eV per Hartree (CODATA 2018) */
+
+typedef struct {
+    double s6, s8, a1, a2_bohr; /* BJ damping of Eq. 2 */
+    double k1, k2, k3;          /* Eq. 4 steepness, covalent-radius scale, Eq. 3 Gaussian width */
+    double rc_disp_A, rc_cn_A;  /* R_pot and R_cn */
+} oracle_params;
+
+typedef struct {
+    int ntypes, max_ref;
+    const int32_t *nref;   /* [ntypes] */
+    const double *cn_ref;  /* [ntypes][max_ref] */
+    const double *c6_ref;  /* [ntypes][ntypes][max_ref][max_ref] */
+    const double *rcov;    /* [ntypes], bohr */
+    const double *sqrtq;   /* [ntypes], bohr */
+} oracle_tables;
+
+typedef struct {
+    int64_t i, j;
+    double d[3]; /* x_j + T - x_i, bohr */
+    double r;
+} instance;
+
+/* ------------------------------------------------------------------ helpers */
+
+static void inv3(const double *H, double *Hi) {
+    double a = H[0], b = H[1], c = H[2], d = H[3], e = H[4], f = H[5], g = H[6], h = H[7], k = H[8];
+    double det = a * (e * k - f * h) - b * (d * k - f * g) + c * (d * h - e * g);
+    Hi[0] = (e * k - f * h) / det; Hi[1] = (c * h - b * k) / det; Hi[2] = (b * f - c * e) / det;
+    Hi[3] = (f * g - d * k) / det; Hi[4] = (a * k - c * g) / det; Hi[5] = (c * d - a * f) / det;
+    Hi[6] = (d * h - e * g) / det; Hi[7] = (b * g - a * h) / det; Hi[8] = (a * e - b * d) / det;
+}
+
+static double det3(const double *H) {
+    return H[0] * (H[4] * H[8] - H[5] * H[7]) - H[1] * (H[3] * H[8] - H[5] * H[6]) +
+           H[2] * (H[3] * H[7] - H[4] * H[6]);
+}
+
+/* Distance between the two lattice planes spanned by rows l and m of H. */
+static double plane_width(const double *H, int k) {
+    int l = (k + 1) % 3, m = (k + 2) % 3;
+    const double *u = H + 3 * l, *v = H + 3 * m;
+    double c0 = u[1] * v[2] - u[2] * v[1], c1 = u[2] * v[0] - u[0] * v[2], c2 = u[0] * v[1] - u[1] * v[0];
+    return fabs(det3(H)) / sqrt(c0 * c0 + c1 * c1 + c2 * c2);
+}
+
+/* Eq. 4 counting function and its derivative d/dr. */
+static double cn_term(double r, double rc_eff, double k1) {
+    return 1.0 / (1.0 + exp(-k1 * (rc_eff / r - 1.0)));
+}
+static double cn_term_dr(double r, double rc_eff, double k1) {
+    double f = cn_term(r, rc_eff, k1);
+    return -k1 * rc_eff / (r * r) * f * (1.0 - f);
+}
+
+/* Normalised Gaussian weights of Eq. 3 for one atom (max-shifted exponents)
+ * and their derivatives with respect to the atom's coordination number. */
+static void ref_weights(const oracle_tables *t, int ti, double n, double k3, double *W, double *dW) {
+    int R = t->max_ref, nr = t->nref[ti];
+    double ex[64], emax = -INFINITY, sum = 0.0;
+    for (int a = 0; a < nr; ++a) {
+        double z = n - t->cn_ref[ti * R + a];
+        ex[a] = -k3 * z * z;
+        if (ex[a] > emax) emax = ex[a];
+    }
+    for (int a = 0; a < R; ++a) W[a] = dW[a] = 0.0;
+    for (int a = 0; a < nr; ++a) {
+        W[a] = exp(ex[a] - emax);
+        sum += W[a];
+    }
+    for (int a = 0; a < nr; ++a) W[a] /= sum;
+    /* dW_a/dn = W_a * (g_a - sum_b W_b g_b), g_a = d(exponent_a)/dn = -2 k3 (n - nref_a) */
+    double gbar = 0.0;
+    for (int a = 0; a < nr; ++a) gbar += W[a] * (-2.0 * k3 * (n - t->cn_ref[ti * R + a]));
+    for (int a = 0; a < nr; ++a) dW[a] = W[a] * (-2.0 * k3 * (n - t->cn_ref[ti * R + a]) - gbar);
+}
+
+/* ------------------------------------------------------------------ instance search */
+
+/* All ordered instances (i, j, T) with r < rc (bohr).  x holds wrapped positions
+ * in bohr; m[k] is the image range along lattice vector k.  Brute force: every
+ * atom pair and every translation in the range.  Each atom's instances are
+ * collected in its own growable row, then the rows are concatenated in atom
+ * order. */
+static instance *find_instances(int64_t n, const double *x, const double *Hb, const int *m, double rc,
+                                int64_t *count_out) {
+    instance **rows = (instance **)calloc((size_t)(n > 0 ? n : 1), sizeof(instance *));
+    int64_t *cnt = (int64_t *)calloc((size_t)(n > 0 ? n : 1), sizeof(int64_t));
+    double rc2 = rc * rc;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t c = 0, cap = 64;
+        instance *row = (instance *)malloc((size_t)cap * sizeof(instance));
+        for (int64_t j = 0; j < n; ++j)
+            for (int n0 = -m[0]; n0 <= m[0]; ++n0)
+                for (int n1 = -m[1]; n1 <= m[1]; ++n1)
+                    for (int n2 = -m[2]; n2 <= m[2]; ++n2) {
+                        if (i == j && n0 == 0 && n1 == 0 && n2 == 0) continue;
+                        double d[3], d2 = 0.0;
+                        for (int a = 0; a < 3; ++a) {
+                            double T = n0 * Hb[a] + n1 * Hb[3 + a] + n2 * Hb[6 + a];
+                            d[a] = x[3 * j + a] + T - x[3 * i + a];
+                            d2 += d[a] * d[a];
+                        }
+                        if (d2 < rc2) {
+                            if (c == cap) {
+                                cap *= 2;
+                                row = (instance *)realloc(row, (size_t)cap * sizeof(instance));
+                            }
+                            instance *q = &row[c++];
+                            q->i = i; q->j = j;
+                            q->d[0] = d[0]; q->d[1] = d[1]; q->d[2] = d[2];
+                            q->r = sqrt(d2);
+                        }
+                    }
+        rows[i] = row;
+        cnt[i] = c;
+    }
+    int64_t total = 0;
+    for (int64_t i = 0; i < n; ++i) total += cnt[i];
+    instance *out = (instance *)malloc((size_t)(total > 0 ? total : 1) * sizeof(instance));
+    int64_t o = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (cnt[i]) memcpy(out + o, rows[i], (size_t)cnt[i] * sizeof(instance));
+        o += cnt[i];
+        free(rows[i]);
+    }
+    free(rows);
+    free(cnt);
+    *count_out = total;
+    return out;
+}
+
+/* ------------------------------------------------------------------ main entry */
+
+/*
+ * d3_oracle_compute: one structure.
+ *   pos     [n][3] Angstrom          types [n] (0 <= t < ntypes)
+ *   cell    [9] rows = lattice vectors, Angstrom     pbc [3]
+ * Outputs (any may be NULL except E):
+ *   E       total energy, eV
+ *   F       [n][3] forces, eV/A
+ *   W       [9] virial, eV (row-major 3x3)
+ *   e_atom  [n] site energies U_i of Eq. 2, eV
+ *   cn      [n] coordination numbers of Eq. 4
+ *   dEdn    [n] dE/dn_i, eV
+ *   dEdp    [4] dE/d(s6, s8, a1, a2) with a2 in bohr, eV (per unit parameter)
+ * Returns 0 on success, negative on bad input.
+ */
+int d3_oracle_compute(const oracle_params *p, const oracle_tables *t, int64_t n, const double *pos,
+                      const int32_t *types, const double *cell, const int32_t *pbc, double *E, double *F,
+                      double *W, double *e_atom, double *cn, double *dEdn_out, double *dEdp) {
+    if (n < 0 || !p || !t || !E) return -1;
+    for (int64_t i = 0; i < n; ++i)
+        if (types[i] < 0 || types[i] >= t->ntypes) return -2;
+    const int R = t->max_ref;
+    const double rcd = p->rc_disp_A / ORACLE_BOHR_A, rcn = p->rc_cn_A / ORACLE_BOHR_A;
+    const double rmax = rcd > rcn ? rcd : rcn;
+
+    /* lattice in bohr, wrapped positions in bohr */
+    double Hb[9], Hi[9];
+    for (int k = 0; k < 9; ++k) Hb[k] = cell[k] / ORACLE_BOHR_A;
+    if (fabs(det3(Hb)) < 1e-12) return -3;
+    inv3(Hb, Hi);
+    double *x = (double *)malloc((size_t)(3 * (n > 0 ? n : 1)) * sizeof(double));
+    for (int64_t i = 0; i < n; ++i) {
+        double xb[3] = {pos[3 * i] / ORACLE_BOHR_A, pos[3 * i + 1] / ORACLE_BOHR_A, pos[3 * i + 2] / ORACLE_BOHR_A};
+        double f[3];
+        for (int k = 0; k < 3; ++k) f[k] = xb[0] * Hi[k] + xb[1] * Hi[3 + k] + xb[2] * Hi[6 + k];
+        for (int k = 0; k < 3; ++k)
+            if (pbc[k]) {
+                f[k] -= floor(f[k]);
+                if (f[k] >= 1.0) f[k] -= 1.0; /* keep [0, 1) when the subtraction rounds up */
+            }
+        for (int a = 0; a < 3; ++a) x[3 * i + a] = f[0] * Hb[a] + f[1] * Hb[3 + a] + f[2] * Hb[6 + a];
+    }
+    /* translations needed: with wrapped fractional coordinates in [0,1) the
+     * fractional separation along k is below 1, and an instance closer than
+     * rmax has |dfrac_k + n_k| <= rmax / width_k, so |n_k| <= ceil(rmax / width_k) */
+    int m[3];
+    for (int k = 0; k < 3; ++k) m[k] = pbc[k] ? (int)ceil(rmax / plane_width(Hb, k)) : 0;
+
+    int64_t ni = 0;
+    instance *I = find_instances(n, x, Hb, m, rmax, &ni);
+
+    /* Eq. 4: coordination numbers */
+    double *nc = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+    for (int64_t q = 0; q < ni; ++q) {
+        const instance *s = &I[q];
+        if (s->r < rcn) {
+            double rc_eff = p->k2 * (t->rcov[types[s->i]] + t->rcov[types[s->j]]);
+            nc[s->i] += cn_term(s->r, rc_eff, p->k1);
+        }
+    }
+
+    /* Eq. 3: per-atom reference weights */
+    double *Wt = (double *)calloc((size_t)(R * (n > 0 ? n : 1)), sizeof(double));
+    double *dWt = (double *)calloc((size_t)(R * (n > 0 ? n : 1)), sizeof(double));
+    for (int64_t i = 0; i < n; ++i) ref_weights(t, types[i], nc[i], p->k3, Wt + R * i, dWt + R * i);
+
+    /* Eq. 2: energy, dE/dn, direct forces and virial, and the parameter derivatives */
+    double Etot = 0.0, dp[4] = {0, 0, 0, 0}, Wv[9] = {0};
+    double *eat = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+    double *dEdn = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+    double *Fb = (double *)calloc((size_t)(3 * (n > 0 ? n : 1)), sizeof(double));
+    for (int64_t q = 0; q < ni; ++q) {
+        const instance *s = &I[q];
+        if (!(s->r < rcd)) continue;
+        int ti = types[s->i], tj = types[s->j];
+        const double *cref = t->c6_ref + ((size_t)(ti * t->ntypes + tj) * R) * R;
+        double C6 = 0.0, dC6i = 0.0, dC6j = 0.0;
+        for (int a = 0; a < R; ++a)
+            for (int b = 0; b < R; ++b) {
+                double c = cref[a * R + b];
+                C6 += Wt[R * s->i + a] * Wt[R * s->j + b] * c;
+                dC6i += dWt[R * s->i + a] * Wt[R * s->j + b] * c;
+                dC6j += Wt[R * s->i + a] * dWt[R * s->j + b] * c;
+            }
+        double R0sq = 3.0 * t->sqrtq[ti] * t->sqrtq[tj];
+        double R0 = sqrt(R0sq);
+        double Rd = p->a1 * R0 + p->a2_bohr;
+        double C8 = C6 * R0sq;
+        double r = s->r, r2 = r * r, r6 = r2 * r2 * r2, r8 = r6 * r2;
+        double R6 = pow(Rd, 6.0), R8 = pow(Rd, 8.0);
+        double d6 = r6 + R6, d8 = r8 + R8;
+        /* this ordered instance carries half of the pair energy */
+        double e = -0.5 * (p->s6 * C6 / d6 + p->s8 * C8 / d8);
+        Etot += e;
+        eat[s->i] += e;
+        /* de/dC6 (C8 follows C6) */
+        double de_dC6 = -0.5 * (p->s6 / d6 + p->s8 * R0sq / d8);
+        dEdn[s->i] += de_dC6 * dC6i;
+        dEdn[s->j] += de_dC6 * dC6j;
+        /* de/dr */
+        double de_dr = 0.5 * (p->s6 * C6 * 6.0 * r * r2 * r2 / (d6 * d6) + p->s8 * C8 * 8.0 * r6 * r / (d8 * d8));
+        for (int a = 0; a < 3; ++a) {
+            double g = de_dr * s->d[a] / r; /* de/dd_a; dd/dx_i = -1, dd/dx_j = +1 */
+            Fb[3 * s->i + a] += g;
+            Fb[3 * s->j + a] -= g;
+            for (int b = 0; b < 3; ++b) Wv[3 * a + b] -= s->d[a] * de_dr * s->d[b] / r;
+        }
+        /* parameter derivatives of this half pair energy */
+        dp[0] += -0.5 * C6 / d6;
+        dp[1] += -0.5 * C8 / d8;
+        double de_dR = 0.5 * (p->s6 * C6 * 6.0 * pow(Rd, 5.0) / (d6 * d6) + p->s8 * C8 * 8.0 * pow(Rd, 7.0) / (d8 * d8));
+        dp[2] += de_dR * R0;
+        dp[3] += de_dR;
+    }
+    /* chain rule through the coordination numbers (Eq. 4 inside Eq. 3) */
+    for (int64_t q = 0; q < ni; ++q) {
+        const instance *s = &I[q];
+        if (!(s->r < rcn)) continue;
+        double rc_eff = p->k2 * (t->rcov[types[s->i]] + t->rcov[types[s->j]]);
+        double g_r = dEdn[s->i] * cn_term_dr(s->r, rc_eff, p->k1); /* d(E via n_i)/dr */
+        for (int a = 0; a < 3; ++a) {
+            double g = g_r * s->d[a] / s->r;
+            Fb[3 * s->i + a] += g;
+            Fb[3 * s->j + a] -= g;
+            for (int b = 0; b < 3; ++b) Wv[3 * a + b] -= s->d[a] * g_r * s->d[b] / s->r;
+        }
+    }
+
+    const double eV = ORACLE_HARTREE_EV, eV_A = ORACLE_HARTREE_EV / ORACLE_BOHR_A;
+    *E = Etot * eV;
+    if (F)
+        for (int64_t i = 0; i < 3 * n; ++i) F[i] = Fb[i] * eV_A;
+    if (W)
+        for (int k = 0; k < 9; ++k) W[k] = Wv[k] * eV;
+    if (e_atom)
+        for (int64_t i = 0; i < n; ++i) e_atom[i] = eat[i] * eV;
+    if (cn)
+        for (int64_t i = 0; i < n; ++i) cn[i] = nc[i];
+    if (dEdn_out)
+        for (int64_t i = 0; i < n; ++i) dEdn_out[i] = dEdn[i] * eV;
+    if (dEdp)
+        for (int k = 0; k < 4; ++k) dEdp[k] = dp[k] * eV;
+
+    free(x); free(I); free(nc); free(Wt); free(dWt); free(eat); free(dEdn); free(Fb);
+    return 0;
+}
+
+/* Eq. 3 weights for one atom, exposed for unit checks. */
+void d3_oracle_weights(const oracle_tables *t, int ti, double n, double k3, double *W, double *dW) {
+    ref_weights(t, ti, n, k3, W, dW);
+}
+
+int d3_oracle_num_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

@@ -1,0 +1,350 @@
+#!/usr/bin/env python
+"""D3(BJ) E + F + virial throughput on GB300 (atom-steps/s).
+
+Workload: the bilayer-graphene binding/sliding scan, 128 structures of 1,440
+C atoms (184,320 atoms) in one batched call, mixed precision.  One step = one
+full pass of the pipeline over the batch: neighbour build (cell lists,
+periodic images, per-atom lists), coordination numbers (Eq. 4), reference
+weights (Eq. 3), dispersion pass (Eq. 2), coordination-number chain rule and
+per-structure sums -- nothing is reused between steps.  The FP64 form is
+timed on the same batch.  Inputs are synthetic (seeded generator).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+N > 1 runs under torchrun: each rank evaluates its own copy of the batch
+(independent structures; no collective on the data path) and the value is the
+atoms of all ranks divided by the slowest rank's time.
+``--impl reference`` times the FP64 CPU oracle on a bounded sample of the
+same workload (the only reference that exists for this method here).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "D3(BJ) E+F+virial atom-steps/s, 1 GB300, mixed vs FP64 form; % of roofline"
+UNIT = "atom-steps/s"
+L2_BYTES = 129 * 1024 * 1024
+# FP32 work the method needs per unique dispersion pair (half-list count, FMA = 2 FLOP):
+# distance 3 + r^2 5 + powers 3 + denominators 2 + reciprocals 2 + C6 and its two CN
+# derivatives 6*Nref + damping sum 3 + energy 2 + dE/dn (both atoms) 4 + force scalar 8
+# + force vector and both atoms' sums 9 + symmetric virial 12 = 53 + 6*Nref.
+def disp_flops_per_pair(nref: int) -> int:
+    return 53 + 6 * nref
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.p = None
+        self.path = os.path.join("/tmp", f"d3gb_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def time_steps(torch, fn, steps, warmup, flush=None, stream=None):
+    """Per-step CUDA-event times (ms) with an untimed L2 flush between steps."""
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(steps):
+        if flush is not None:
+            flush()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        times.append(a.elapsed_time(b))
+    return times
+
+
+def count_pairs(torch, batch, rc, dev):
+    """Unique pairs within rc over the whole batch (bookkeeping for the roofline
+    denominator).  Minimum image is exact here: every cell edge exceeds 2 rc in
+    the plane, and along z the vacuum keeps all periodic images beyond rc."""
+    tot = 0
+    for s in range(batch.nstruct):
+        pos, _, cell, _ = batch.structure(s)
+        L = torch.tensor(np.diag(cell), dtype=torch.float64, device=dev)
+        assert np.allclose(cell, np.diag(np.diag(cell)))
+        x = torch.tensor(pos, dtype=torch.float64, device=dev)
+        d = x[:, None, :] - x[None, :, :]
+        d = d - L * torch.round(d / L)
+        r2 = (d * d).sum(-1)
+        tot += int(((r2 < rc * rc) & (r2 > 0)).sum().item()) // 2
+    return tot
+
+
+def cpu_baseline(batch, params, budget_s=15.0):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload's structures."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    oracle.compute(*batch.structure(0), batch.tables, params)
+    one = time.perf_counter() - t0
+    nsamp = int(max(1, min(batch.nstruct - 1, budget_s / max(one, 1e-3))))
+    idx = list(np.linspace(1, batch.nstruct - 1, nsamp).astype(int))
+    t0 = time.perf_counter()
+    atoms = 0
+    for s in idx:
+        r = oracle.compute(*batch.structure(s), batch.tables, params)
+        atoms += len(batch.structure(s)[0])
+    dt = time.perf_counter() - t0
+    return {"value": atoms / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{len(idx)} of {batch.nstruct} structures ({atoms} atom-steps, {dt:.1f} s), FP64 C/OpenMP"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    from paper_2310_05279_gb300 import workloads as wl
+    if rank != 0:
+        return 0
+    batch = wl.bilayer_scan()
+    params = dict(wl.PBE_BJ)
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    oracle.compute(*batch.structure(0), batch.tables, params)
+    one = time.perf_counter() - t0
+    budget = max(0.5, 120.0 / max(1, args.steps))  # seconds of oracle work per step
+    per_step = max(1, min(batch.nstruct, int(budget / max(one, 1e-3))))
+    idx = list(np.linspace(0, batch.nstruct - 1, per_step).astype(int))
+    for _ in range(args.warmup):
+        oracle.compute(*batch.structure(idx[0]), batch.tables, params)
+    times, atoms = [], 0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        a = 0
+        for s in idx:
+            oracle.compute(*batch.structure(s), batch.tables, params)
+            a += len(batch.structure(s)[0])
+        times.append(time.perf_counter() - t0)
+        atoms = a
+    value = atoms / statistics.mean(times)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "bilayer_scan 128 x 1440 C atoms (sampled per step)", "sample_structures": len(idx),
+                       "atoms_per_step": atoms, "parallelism": "OpenMP host threads"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": f"{len(idx)} of {batch.nstruct} structures per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+
+    from paper_2310_05279_gb300 import D3, workloads as wl
+    from paper_2310_05279_gb300 import build as libbuild
+    libbuild.build()
+    batch = wl.bilayer_scan()
+    N = batch.natoms
+    params = dict(wl.PBE_BJ)
+    pos = torch.tensor(batch.pos, dtype=torch.float64, device=dev)
+    typ = torch.tensor(batch.types, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+    flush_buf = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def flush():
+        flush_buf.fill_(1.0)
+
+    d3 = D3(batch.tables, params, precision="mixed")
+    out = d3.compute_batch(pos, typ, batch.offsets, batch.cells, batch.pbc)
+    d3.sync_status()
+
+    def step():
+        d3.compute_batch(pos, typ, batch.offsets, batch.cells, batch.pbc, out=out)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    d3.profile_reset()
+    d3.profile(True)
+    clk = ClockSampler(dev.index)
+    clk.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    times = time_steps(torch, step, args.steps, 0, flush=flush, stream=stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = clk.stop()
+    prof = d3.profile_read()
+    d3.profile(False)
+    d3.sync_status()
+    ms = sum(times) / len(times)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * N / (ms * 1e-3)
+
+    # dominant kernel: the dispersion pass (Eq. 2), timed by events on the launching stream
+    stage_ms = {k: prof["ms"][k] / max(1, prof["calls"][k]) for k in prof["ms"]}
+    dom = max(stage_ms, key=lambda k: stage_ms[k])
+    launches_per_step = prof["launches"] / max(1, args.steps)
+
+    # FP64 form on the same batch
+    d3f = D3(batch.tables, params, precision="fp64")
+    outf = d3f.compute_batch(pos, typ, batch.offsets, batch.cells, batch.pbc)
+    d3f.sync_status()
+    d3f.profile(True)
+    tf = time_steps(torch, lambda: d3f.compute_batch(pos, typ, batch.offsets, batch.cells, batch.pbc, out=outf),
+                    args.fp64_steps, 1, flush=flush, stream=stream)
+    proff = d3f.profile_read()
+    d3f.profile(False)
+    msf = sum(tf) / len(tf)
+    del d3f
+
+    # end to end through the host-memory entry point (pinned buffers, copies inside)
+    pin_pos = torch.tensor(batch.pos, dtype=torch.float64).pin_memory()
+    pin_typ = torch.tensor(batch.types, dtype=torch.int32).pin_memory()
+    hout = dict(E=torch.empty(batch.nstruct, dtype=torch.float64).pin_memory(),
+                F=torch.empty((N, 3), dtype=torch.float64).pin_memory(),
+                W=torch.empty((batch.nstruct, 3, 3), dtype=torch.float64).pin_memory())
+    for _ in range(2):
+        d3.compute_batch_host(pin_pos, pin_typ, batch.offsets, batch.cells, batch.pbc, out=hout)
+    e2e_t = []
+    for _ in range(max(3, args.steps // 2)):
+        flush()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        d3.compute_batch_host(pin_pos, pin_typ, batch.offsets, batch.cells, batch.pbc, out=hout)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_val = world * N / statistics.mean(e2e_t)
+    h2d = N * 3 * 8 + N * 4
+    d2h = batch.nstruct * 8 + N * 3 * 8 + batch.nstruct * 9 * 8
+
+    # roofline of the dispersion pass: FP32 pipe, FMA = 2 FLOP
+    peaks, peak_kind = measured_peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sm_count = props.multi_processor_count
+    fmax = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    fp32_peak = sm_count * 128 * 2 * fmax / 1e12  # TFLOP/s
+    pairs = count_pairs(torch, batch, params["rc_disp"], dev)
+    nref = int(batch.tables.max_ref)
+    disp_tflops = disp_flops_per_pair(nref) * pairs / (stage_ms["disp"] * 1e-3) / 1e12
+    roof = {"bound": "alu", "kernel": "k_disp (dispersion pass, Eq. 2)", "achieved": disp_tflops,
+            "peak": fp32_peak, "unit": "TFLOP/s", "frac": disp_tflops / fp32_peak, "traffic": None,
+            "peak_source": f"{sm_count} SMs x 128 FP32 lanes x 2 x {fmax/1e6:.0f} MHz (sm_max_mhz, {peak_kind})",
+            "algorithmic": f"{disp_flops_per_pair(nref)} FLOP per unique pair within 12 A x {pairs:.4g} pairs"}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "bilayer_scan: 128 AB-graphene bilayers x 1440 C atoms (184,320 atoms), "
+                                   "d 2.8-8.0 A x 8 slides", "structures": batch.nstruct, "atoms": N,
+                       "precision": "mixed (FP32 pair math, FP64 accumulation)", "rc_disp_A": 12.0, "rc_cn_A": 6.0,
+                       "neighbour_build": "every step", "l2": "flushed between timed steps",
+                       "parallelism": f"replica per GPU x{world}"},
+            "roofline": roof,
+            "stage_ms": stage_ms, "dominant_stage": dom,
+            "fp64_form": {"value": world * N / (msf * 1e-3), "unit": UNIT, "ms_per_step": msf, "dtype": "f64",
+                          "stage_ms": {k: proff["ms"][k] / max(1, proff["calls"][k]) for k in proff["ms"]},
+                          "mixed_speedup": msf / ms},
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "entry_point": "d3_compute_batch_host (pinned host buffers)"},
+            "gpu_launches": int(round(launches_per_step * args.steps)),
+            "gpu_launches_per_step": launches_per_step,
+            "clocks": clocks}
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(batch, params)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,185 @@
+/*
+ * d3gb.h -- C ABI of the GB300 D3(BJ) dispersion library.
+ *
+ * The library evaluates the environment-dependent D3 dispersion correction with
+ * Becke-Johnson damping as used in NEP-D3 (Ying & Fan, arXiv 2310.05279,
+ * Sec. II A): the total energy of Eq. 1 as a sum of the site energies of Eq. 2,
+ * the C6 interpolation of Eq. 3 over the coordination numbers of Eq. 4, the
+ * forces of Eqs. 5-6 (evaluated as F = -dE/dx including the dependence on
+ * neighbours' coordination numbers) and the total of the per-atom virials of
+ * Eq. 7.  The three-body term is excluded, as in the paper.
+ *
+ * Conventions shared by every entry point
+ *  - Units: positions and cells in Angstrom; a2, covalent radii and sqrt(Q) in
+ *    bohr; C6 references in Hartree*bohr^6.  Outputs: E in eV, F in eV/A,
+ *    W in eV.  Internally everything is evaluated in bohr/Hartree
+ *    (1 bohr = 0.529177210903 A, 1 Ha = 27.211386245988 eV).
+ *  - Cell matrices are row-major 3x3 with rows = lattice vectors.  pbc[k] = 0
+ *    means no periodic images along lattice vector k.
+ *  - Batches are concatenated: structure s owns atoms [offsets[s], offsets[s+1]).
+ *  - Pointer spaces are stated per argument: "device" pointers must be CUDA
+ *    device (or managed) memory on the current device; "host" pointers are
+ *    ordinary host memory.  The caller owns every input and output buffer; the
+ *    library owns the handle, its tables, neighbour lists and workspace.
+ *  - Work is enqueued on the caller's stream (a cudaStream_t passed as void*;
+ *    NULL = legacy default stream).  Unless stated otherwise a call does not
+ *    synchronise.  The first call for a new batch geometry (offsets, cells,
+ *    pbc) sizes the workspace and synchronises once; later calls with the same
+ *    geometry allocate nothing and do not synchronise, so they can be captured
+ *    in a CUDA graph.
+ *  - Errors: every call returns a d3_status.  Device-side problems (capacity
+ *    overflow, non-finite coordinates, bad types) are recorded in a status word
+ *    that d3_sync_status() reads.  The library never aborts or traps.
+ *  - Thread safety: one handle must not be used from two host threads at once.
+ */
+#ifndef D3GB_H
+#define D3GB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum d3_status {
+    D3_OK = 0,
+    D3_ERR_ARG = 1,       /* invalid argument: NULL pointer, negative size, degenerate cell, bad table */
+    D3_ERR_CUDA = 2,      /* a CUDA runtime call failed (message in d3_last_error) */
+    D3_ERR_CAPACITY = 3,  /* a neighbour or image buffer overflowed; it has been regrown, repeat the call */
+    D3_ERR_NONFINITE = 4, /* a coordinate was NaN or infinite */
+    D3_ERR_TIMEOUT = 5,   /* a bounded device wait gave up */
+    D3_ERR_TYPE = 6,      /* an atom type outside [0, ntypes) */
+    D3_ERR_STATE = 7      /* call out of sequence */
+} d3_status;
+
+/* precision of the pair arithmetic */
+enum { D3_FP64 = 0, D3_MIXED = 1 };
+
+/* Functional parameters of Eq. 2 (s6, s8, a1, a2), the constants of Eqs. 3-4
+ * (k1 = 16, k2 = 4/3 scales the tabulated covalent radii, k3 = 4), and the two
+ * cutoffs R_pot and R_cn of the paper (12 A and 6 A by default).  skin_A is
+ * added to both list radii; 0 rebuilds exact lists every call.
+ * precision: D3_MIXED evaluates distances, damping, the C6 interpolation and
+ * the coordination-number terms in FP32 with FP64 accumulation of energies,
+ * virials and dE/dn; D3_FP64 evaluates everything in FP64. */
+typedef struct d3_params {
+    double s6, s8, a1, a2_bohr;
+    double k1, k2, k3;
+    double rc_disp_A, rc_cn_A, skin_A;
+    int32_t precision;
+} d3_params;
+
+/* Reference data (Eq. 3 and Eq. 4), host memory, copied by d3_create.
+ *  nref[t]                      references of element t (1..max_ref)
+ *  cn_ref[t*max_ref + a]        reference coordination numbers
+ *  c6_ref[((ti*ntypes + tj)*max_ref + a)*max_ref + b]
+ *                               C6 reference grid (Ha*bohr^6); must satisfy
+ *                               c6_ref[ti,tj,a,b] == c6_ref[tj,ti,b,a]
+ *  rcov_bohr[t]                 tabulated covalent radius (Eq. 4 uses k2*rcov)
+ *  sqrtq[t]                     sqrt(Q); R0^2 = 3 sqrtq_i sqrtq_j, C8 = C6 R0^2
+ * Limits: 1 <= ntypes <= 16, 1 <= max_ref <= 7. */
+typedef struct d3_tables {
+    int32_t ntypes, max_ref;
+    const int32_t *nref;
+    const double *cn_ref;
+    const double *c6_ref;
+    const double *rcov_bohr;
+    const double *sqrtq;
+} d3_tables;
+
+typedef struct d3_handle d3_handle;
+
+/* Create a handle: validates and copies params and tables (host pointers) to
+ * the current CUDA device.  *out receives the handle; NULL on failure. */
+d3_status d3_create(const d3_params *params, const d3_tables *tables, d3_handle **out);
+
+/* Free every resource of the handle (synchronises the device first). NULL is a no-op. */
+void d3_destroy(d3_handle *h);
+
+/* Replace the four damping parameters of Eq. 2 (s6, s8, a1, a2 in bohr).
+ * Takes effect for work enqueued afterwards on the handle's last stream. */
+d3_status d3_set_damping(d3_handle *h, double s6, double s8, double a1, double a2_bohr);
+
+/* Build (or rebuild) the neighbour lists of a batch and size the workspace
+ * for it; synchronises.  The cell-list build: wrap into the cell, periodic
+ * image atoms within the list radius, counting sort by cell, and per-atom
+ * lists within R_pot and R_cn (Eqs. 2 and 4 sum over neighbours within these
+ * cutoffs).
+ *  B        number of structures (>= 0)
+ *  offsets  host int64[B+1], offsets[0] = 0, non-decreasing
+ *  pos      device double[N][3], A        types  device int32[N]
+ *  cells    host double[B][9], A          pbc    host int32[B][3]  */
+d3_status d3_build_neighbors(d3_handle *h, int32_t B, const int64_t *offsets, const double *pos,
+                             const int32_t *types, const double *cells, const int32_t *pbc, void *stream);
+
+/* One structure of n atoms: energy E (device double[1], eV), forces F (device
+ * double[n][3], eV/A) and virial W (device double[9], eV, symmetric,
+ * W = -dE/d(strain) = sum over atoms of Eq. 7).  cell: host double[9];
+ * pbc: host int32[3].  Equivalent to d3_compute_batch with B = 1. */
+d3_status d3_compute(d3_handle *h, const double *pos, const int32_t *types, int64_t n, const double *cell,
+                     const int32_t *pbc, double *E, double *F, double *W, void *stream);
+
+/* A batch of B independent structures in one pass: E device double[B],
+ * F device double[N][3] in input order, W device double[B][9]. */
+d3_status d3_compute_batch(d3_handle *h, int32_t B, const int64_t *offsets, const double *pos,
+                           const int32_t *types, const double *cells, const int32_t *pbc, double *E, double *F,
+                           double *W, void *stream);
+
+/* As d3_compute_batch, plus optional per-atom outputs (device, input order;
+ * NULL to skip): e_atom double[N] site energies U_i of Eq. 2 in eV, cn
+ * double[N] coordination numbers of Eq. 4. */
+d3_status d3_compute_batch_ex(d3_handle *h, int32_t B, const int64_t *offsets, const double *pos,
+                              const int32_t *types, const double *cells, const int32_t *pbc, double *E,
+                              double *F, double *W, double *e_atom, double *cn, void *stream);
+
+/* As d3_compute_batch with every array in HOST memory (page-locked memory
+ * gives full copy speed): copies inputs to the device, computes, copies E, F,
+ * W back and synchronises the stream before returning. */
+d3_status d3_compute_batch_host(d3_handle *h, int32_t B, const int64_t *offsets, const double *pos,
+                                const int32_t *types, const double *cells, const int32_t *pbc, double *E,
+                                double *F, double *W, void *stream);
+
+/* Hand-written backward of (E, F) for refitting the damping parameters.
+ * Given upstream gradients dL/dE (device double[B], per eV) and dL/dF
+ * (device double[N][3], per eV/A) it returns
+ *   dLdparams  device double[4] = dL/d(s6, s8, a1, a2[bohr])
+ *   dLdpos     device double[N][3] = dL/dx (per A), input order
+ * The force term needs the Hessian-vector product H*(dL/dF); it is formed by
+ * forward-mode differentiation of the whole force evaluation along dL/dF
+ * (coordination numbers recomputed, no per-pair storage), in FP64.
+ * Either output may be NULL.  Inputs as in d3_compute_batch. */
+d3_status d3_backward(d3_handle *h, int32_t B, const int64_t *offsets, const double *pos, const int32_t *types,
+                      const double *cells, const int32_t *pbc, const double *dLdE, const double *dLdF,
+                      double *dLdparams, double *dLdpos, void *stream);
+
+/* Synchronise the handle's last stream and report the first recorded
+ * device-side problem (then clear it). */
+d3_status d3_sync_status(d3_handle *h);
+
+/* Human-readable description of the last error on this handle ("" if none). */
+const char *d3_last_error(const d3_handle *h);
+
+/* Stage timing for benchmarks and profiling.  While enabled, every later
+ * compute call brackets its stages with CUDA events on the call's stream:
+ * 0 neighbour build, 1 coordination numbers (Eq. 4), 2 reference weights
+ * (Eq. 3), 3 dispersion pass (Eq. 2), 4 coordination-number chain rule,
+ * 5 per-structure sums.  Events are cheap stream markers; they add no
+ * synchronisation.  The library also counts every kernel it launches. */
+d3_status d3_profile_enable(d3_handle *h, int32_t on);
+
+/* Synchronise on the recorded events and return totals since the last reset:
+ * ms[6] milliseconds per stage and calls[6] calls timed per stage (either may
+ * be NULL); *launches = kernels launched by the library (may be NULL). */
+d3_status d3_profile_read(d3_handle *h, double *ms, int64_t *calls, int64_t *launches);
+
+/* Zero the stage totals and the launch counter. */
+d3_status d3_profile_reset(d3_handle *h);
+
+/* Library version string. */
+const char *d3_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* D3GB_H */

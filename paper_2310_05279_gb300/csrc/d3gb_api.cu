@@ -1,0 +1,762 @@
+// d3gb_api.cu -- C ABI, handle and per-geometry plan of the D3(BJ) library.
+//
+// A plan holds everything that depends only on the batch geometry (offsets,
+// cells, pbc): the per-structure cell grids and image ranges, and device
+// buffers sized for them.  The first call for a new geometry runs the
+// neighbour build once synchronously to measure image and neighbour counts
+// and regrows the buffers if the estimates were short; every later call with
+// the same geometry only enqueues kernels.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/d3gb.h"
+#include "d3gb_internal.cuh"
+
+namespace d3gb {
+cudaError_t launch_build_impl(const Work& w, const double* pos, const int32_t* types, const double* rk_tab,
+                              int* bsum, cudaStream_t st);
+int64_t scan_scratch_ints(int64_t ncells);
+cudaError_t launch_backward(const Work& w, const Consts& c, const double* c6d, const dbl4* paird,
+                            const double* cnref, const int* nref, const double* dLdE, const double* dLdF,
+                            double* dLdp, double* dLdx, double* scratch, int B, cudaStream_t st);
+int64_t backward_scratch_doubles(const Work& w, int B);
+}  // namespace d3gb
+
+using namespace d3gb;
+
+namespace {
+
+constexpr int kWindowCells = 3;  // list radius spans at most this many cells per axis
+
+struct DevBuf {
+    std::vector<void*> ptrs;
+    template <class T>
+    cudaError_t alloc(T** p, size_t n) {
+        *p = nullptr;
+        if (n == 0) n = 1;
+        cudaError_t e = cudaMalloc((void**)p, n * sizeof(T));
+        if (e == cudaSuccess) ptrs.push_back((void*)*p);
+        return e;
+    }
+    void release() {
+        for (void* p : ptrs) cudaFree(p);
+        ptrs.clear();
+    }
+};
+
+struct Plan {
+    bool valid = false, sized = false;
+    int B = 0;
+    std::vector<int64_t> offsets;
+    std::vector<double> cells;
+    std::vector<int32_t> pbc;
+    std::vector<StructGeo> geo;
+    int64_t Nr = 0, ncells = 0, list_disp = 0, list_cn = 0;
+    int ghost_cap = 0;
+    DevBuf mem;
+    Work w{};
+    int* bsum = nullptr;  // scan scratch
+    double* bwd_scratch = nullptr;
+    int64_t bwd_scratch_n = 0;
+};
+
+}  // namespace
+
+struct d3_handle {
+    d3_params prm{};
+    int T = 0, R = 0, RP = 0;
+    std::vector<int32_t> nref;
+    std::vector<double> cnref, c6, rcov, sqrtq;
+    DevBuf tabmem;
+    int* d_nref = nullptr;
+    double* d_cnref = nullptr;
+    float* d_c6f = nullptr;
+    double* d_c6d = nullptr;
+    float4* d_pairf = nullptr;
+    dbl4* d_paird = nullptr;
+    dbl4* d_pairb = nullptr;  // (R0, R, R0^2, 0) per element pair, for the backward
+    float4* d_rcpair = nullptr;  // k2 (Rcov_i + Rcov_j) and its square, FP32 hi + lo
+    double* d_rk = nullptr;
+    int* d_status = nullptr;
+    cudaStream_t last_stream = nullptr;
+    std::string err;
+    Plan plan;
+    // staging buffers of the host-memory entry point
+    DevBuf stage;
+    size_t stage_atoms = 0, stage_structs = 0;
+    double *s_pos = nullptr, *s_E = nullptr, *s_F = nullptr, *s_W = nullptr;
+    int32_t* s_types = nullptr;
+    // stage timing (d3_profile_*): 7 events per call, read back lazily
+    bool prof_on = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::vector<cudaEvent_t>> ev_pending;
+    double prof_ms[6] = {0, 0, 0, 0, 0, 0};
+    int64_t prof_calls[6] = {0, 0, 0, 0, 0, 0};
+    int64_t launches = 0;
+};
+
+namespace {
+
+d3_status fail(d3_handle* h, d3_status s, const std::string& msg) {
+    if (h) h->err = msg;
+    return s;
+}
+
+d3_status cuda_fail(d3_handle* h, cudaError_t e, const char* where) {
+    return fail(h, D3_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+void inv3(const double* H, double* Hi) {
+    const double a = H[0], b = H[1], c = H[2], d = H[3], e = H[4], f = H[5], g = H[6], hh = H[7], k = H[8];
+    const double det = a * (e * k - f * hh) - b * (d * k - f * g) + c * (d * hh - e * g);
+    Hi[0] = (e * k - f * hh) / det; Hi[1] = (c * hh - b * k) / det; Hi[2] = (b * f - c * e) / det;
+    Hi[3] = (f * g - d * k) / det;  Hi[4] = (a * k - c * g) / det;  Hi[5] = (c * d - a * f) / det;
+    Hi[6] = (d * hh - e * g) / det; Hi[7] = (b * g - a * hh) / det; Hi[8] = (a * e - b * d) / det;
+}
+
+double det3(const double* H) {
+    return H[0] * (H[4] * H[8] - H[5] * H[7]) - H[1] * (H[3] * H[8] - H[5] * H[6]) + H[2] * (H[3] * H[7] - H[4] * H[6]);
+}
+
+// Upload the damping table (R^6, R^8, s6, s8 R0^2 per element pair) in both precisions.
+d3_status upload_pair_table(d3_handle* h) {
+    const int T = h->T;
+    std::vector<dbl4> pd(T * T), pb(T * T);
+    std::vector<float4> pf(T * T);
+    for (int a = 0; a < T; ++a)
+        for (int b = 0; b < T; ++b) {
+            const double R0sq = 3.0 * h->sqrtq[a] * h->sqrtq[b];
+            const double Rd = h->prm.a1 * std::sqrt(R0sq) + h->prm.a2_bohr;
+            const double R2 = Rd * Rd, R6 = R2 * R2 * R2, R8 = R6 * R2;
+            pd[a * T + b] = dbl4_make(R6, R8, h->prm.s6, h->prm.s8 * R0sq);
+            pf[a * T + b] = make_float4((float)R6, (float)R8, (float)h->prm.s6, (float)(h->prm.s8 * R0sq));
+            pb[a * T + b] = dbl4_make(std::sqrt(R0sq), Rd, R0sq, 0.0);
+        }
+    cudaError_t e = cudaMemcpy(h->d_paird, pd.data(), pd.size() * sizeof(dbl4), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(h->d_pairf, pf.data(), pf.size() * sizeof(float4), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(h->d_pairb, pb.data(), pb.size() * sizeof(dbl4), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(h, e, "pair table upload");
+    return D3_OK;
+}
+
+// List radius (bohr) for a cutoff in A: the cutoff plus the skin plus a margin
+// covering the FP32 grid positions the list build compares (<= sqrt(3) 2^-10 bohr).
+double list_radius(const d3_handle* h, double rc_A) {
+    return rc_A / kBohrA * (1.0 + 1e-5) + 4e-3 + std::max(0.0, h->prm.skin_A) / kBohrA;
+}
+
+Consts make_consts(const d3_handle* h) {
+    Consts c{};
+    const double rd = h->prm.rc_disp_A / kBohrA, rn = h->prm.rc_cn_A / kBohrA;
+    c.rc_disp2 = rd * rd;
+    c.rc_cn2 = rn * rn;
+    c.k1 = h->prm.k1;
+    c.k3 = h->prm.k3;
+    c.s6 = h->prm.s6;
+    c.s8 = h->prm.s8;
+    c.a1 = h->prm.a1;
+    c.a2 = h->prm.a2_bohr;
+    c.T = h->T;
+    c.R = h->R;
+    c.RP = h->RP;
+    return c;
+}
+
+bool same_geometry(const Plan& P, int32_t B, const int64_t* offsets, const double* cells, const int32_t* pbc) {
+    if (!P.valid || P.B != B) return false;
+    if (B == 0) return P.offsets.size() == 1;
+    return std::memcmp(P.offsets.data(), offsets, sizeof(int64_t) * (B + 1)) == 0 &&
+           std::memcmp(P.cells.data(), cells, sizeof(double) * 9 * B) == 0 &&
+           std::memcmp(P.pbc.data(), pbc, sizeof(int32_t) * 3 * B) == 0;
+}
+
+// Host geometry of every structure: cell grid over the fractional range
+// [-delta, 1 + delta) along periodic axes (delta = list radius / plane
+// spacing) and [0, 1) along open ones, window half-widths, image ranges and
+// first estimates of the per-atom list lengths.
+d3_status plan_geometry(d3_handle* h, Plan& P, int32_t B, const int64_t* offsets, const double* cells,
+                        const int32_t* pbc, std::vector<double>& ghost_est) {
+    const double rld = list_radius(h, h->prm.rc_disp_A), rln = list_radius(h, h->prm.rc_cn_A);
+    const double rl = std::max(rld, rln);
+    P.geo.assign(B, StructGeo{});
+    ghost_est.assign(B, 0.0);
+    int64_t cell_base = 0;
+    for (int s = 0; s < B; ++s) {
+        StructGeo& G = P.geo[s];
+        for (int k = 0; k < 9; ++k) G.H[k] = cells[9 * s + k] / kBohrA;
+        const double det = det3(G.H);
+        double scale = 0;
+        for (int k = 0; k < 9; ++k) scale = std::max(scale, std::fabs(G.H[k]));
+        if (!(std::fabs(det) > 1e-9 * scale * scale * scale) || !std::isfinite(det))
+            return fail(h, D3_ERR_ARG, "degenerate or non-finite cell for structure " + std::to_string(s));
+        inv3(G.H, G.Hinv);
+        const int64_t n = offsets[s + 1] - offsets[s];
+        if (n < 0) return fail(h, D3_ERR_ARG, "offsets must be non-decreasing");
+        if (n > (int64_t)1 << 27) return fail(h, D3_ERR_ARG, "structure too large (max 2^27 atoms)");
+        double vol_factor = 1.0;
+        int64_t nc_total = 1;
+        for (int k = 0; k < 3; ++k) {
+            const double* u = G.H + 3 * ((k + 1) % 3);
+            const double* v = G.H + 3 * ((k + 2) % 3);
+            const double cx = u[1] * v[2] - u[2] * v[1], cy = u[2] * v[0] - u[0] * v[2], cz = u[0] * v[1] - u[1] * v[0];
+            const double width = std::fabs(det) / std::sqrt(cx * cx + cy * cy + cz * cz);
+            G.pbc[k] = pbc[3 * s + k] ? 1 : 0;
+            if (G.pbc[k]) {
+                const double delta = rl / width + 1e-9;
+                G.img[k] = (int)std::ceil(delta);
+                if (G.img[k] > 100) return fail(h, D3_ERR_ARG, "cell too thin for the cutoff (more than 100 images)");
+                G.lo[k] = -delta;
+                G.ext_lo[k] = -delta;
+                G.ext_hi[k] = 1.0 + delta;
+                vol_factor *= 1.0 + 2.0 * delta;
+            } else {
+                G.img[k] = 0;
+                G.lo[k] = 0.0;
+                G.ext_lo[k] = 0.0;
+                G.ext_hi[k] = 1.0;
+            }
+            const double span = G.pbc[k] ? 1.0 + 2.0 * (-G.lo[k]) : 1.0;
+            long long nck = (long long)std::floor(span * width * kWindowCells / rl);
+            nck = std::max(1LL, std::min(nck, 2048LL));
+            G.ncell[k] = (int)nck;
+            G.fscale[k] = (double)nck / span;
+            const double cw = span * width / (double)nck;
+            G.win[k] = (int)std::min<long long>(nck, (long long)std::ceil(rl / cw));
+            nc_total *= nck;
+        }
+        if (nc_total > ((int64_t)1 << 26)) return fail(h, D3_ERR_ARG, "too many cells for structure " + std::to_string(s));
+        G.cell_base = cell_base;
+        cell_base += nc_total;
+        G.atom_base = offsets[s];
+        G.natoms = (int32_t)n;
+        const double vol = std::fabs(det);  // bohr^3
+        const double rho = n > 0 ? (double)n / vol : 0.0;
+        const double four_thirds_pi = 4.18879020478639;
+        const double nd = four_thirds_pi * rld * rld * rld * rho, nn = four_thirds_pi * rln * rln * rln * rho;
+        const double cap_all = (double)n * vol_factor + 8;
+        G.cap_disp = round_cap(std::min(cap_all, std::ceil(1.3 * nd + 32.0)));
+        G.cap_cn = round_cap(std::min(cap_all, std::ceil(1.3 * nn + 16.0)));
+        ghost_est[s] = (double)n * (vol_factor - 1.0);
+    }
+    P.ncells = cell_base;
+    return D3_OK;
+}
+
+// (Re)allocate every device buffer of the plan for the current capacities.
+d3_status plan_alloc(d3_handle* h, Plan& P) {
+    P.mem.release();
+    P.bwd_scratch = nullptr;
+    P.bwd_scratch_n = 0;
+    const int B = P.B;
+    const int64_t Nr = P.Nr, C = P.ncells, Ng = P.ghost_cap, Nt = Nr + Ng;
+    int64_t ld = 0, lc = 0;
+    for (int s = 0; s < B; ++s) {
+        P.geo[s].list_base_disp = ld;
+        P.geo[s].list_base_cn = lc;
+        ld += list_size(P.geo[s].natoms, P.geo[s].cap_disp);
+        lc += list_size(P.geo[s].natoms, P.geo[s].cap_cn);
+    }
+    P.list_disp = ld;
+    P.list_cn = lc;
+    Work& w = P.w;
+    w = Work{};
+    w.B = B;
+    w.Nr = Nr;
+    w.ncells = C;
+    w.ghost_cap = (int)Ng;
+    w.T = h->T;
+    w.R = h->R;
+    w.RP = h->RP;
+    const size_t rs = h->prm.precision == D3_MIXED ? sizeof(float) : sizeof(double);
+    StructGeo* dgeo = nullptr;
+    int64_t* doff = nullptr;
+    DevBuf& m = P.mem;
+    cudaError_t e = cudaSuccess;
+#define A(ptr, T, n) \
+    if (e == cudaSuccess) e = m.alloc((T**)&(ptr), (size_t)(n))
+    A(dgeo, StructGeo, B);
+    A(doff, int64_t, B + 1);
+    A(w.cnt_real, int, C + 1);
+    A(w.cnt_ghost, int, C + 1);
+    A(w.start_real, int, C + 1);
+    A(w.start_ghost, int, C + 1);
+    A(w.cell_of, int, Nr);
+    A(w.slot_of, int, Nr);
+    A(w.xw, double, 3 * Nr);
+    A(w.ghost_src, int, Ng);
+    A(w.ghost_shift, int, Ng);
+    A(w.ghost_cell, int, Ng);
+    A(w.ghost_slot, int, Ng);
+    A(w.ghost_count, int, 1);
+    A(w.sorted_src, int, Nr);
+    A(w.gsorted, int, Ng);
+    A(w.pos64, dbl4, Nt);
+    A(w.hi, float4, Nt);
+    A(w.lo, float4, Nt);
+    A(w.perm, int, Nr);
+    A(w.sid, int, Nr);
+    A(w.cell_sorted, int, Nr);
+    A(w.nbr_disp, int, ld);
+    A(w.nbr_cn, int, lc);
+    A(w.cnt_disp, int, Nr);
+    A(w.cnt_cn, int, Nr);
+    A(w.maxcnt, int, 2 * B);
+    A(w.cn, double, Nr);
+    A(w.W, char, Nr * h->RP * rs);
+    A(w.dW, char, Nr * h->RP * rs);
+    A(w.v, char, Nr * h->T * h->RP * rs);
+    A(w.dEdn, char, Nr * rs);
+    A(w.Fd, char, Nr * 4 * rs);
+    A(w.eat, double, Nr);
+    A(w.wv, double, 6 * Nr);
+    int64_t maxn = 0;
+    for (int s = 0; s < B; ++s) maxn = std::max<int64_t>(maxn, P.geo[s].natoms);
+    w.max_natoms = maxn;
+    A(w.fin_part, double, 7 * (int64_t)B * std::max<int64_t>(1, (maxn + 4095) / 4096));
+    A(P.bsum, int, scan_scratch_ints(C));
+#undef A
+    if (e != cudaSuccess) {
+        P.mem.release();
+        P.valid = false;
+        return cuda_fail(h, e, "workspace allocation");
+    }
+    P.w.status = h->d_status;
+    P.w.geo = dgeo;
+    P.w.offsets = doff;
+    const double rld = list_radius(h, h->prm.rc_disp_A), rln = list_radius(h, h->prm.rc_cn_A);
+    w.rl_disp2 = (float)(rld * rld);
+    w.rl_cn2 = (float)(rln * rln);
+    e = cudaMemcpy(dgeo, P.geo.data(), sizeof(StructGeo) * B, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(doff, P.offsets.data(), sizeof(int64_t) * (B + 1), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(h, e, "geometry upload");
+    return D3_OK;
+}
+
+std::vector<cudaEvent_t> take_events(d3_handle* h, int n) {
+    std::vector<cudaEvent_t> v;
+    while ((int)v.size() < n) {
+        if (!h->ev_pool.empty()) {
+            v.push_back(h->ev_pool.back());
+            h->ev_pool.pop_back();
+        } else {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) break;
+            v.push_back(e);
+        }
+    }
+    return v;
+}
+
+d3_status enqueue_build(d3_handle* h, Plan& P, const double* pos, const int32_t* types, cudaStream_t st) {
+    Work& w = P.w;
+    cudaError_t e = cudaMemsetAsync(w.cnt_real, 0, sizeof(int) * (P.ncells + 1), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(w.cnt_ghost, 0, sizeof(int) * (P.ncells + 1), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(w.ghost_count, 0, sizeof(int), st);
+    if (e == cudaSuccess && P.B > 0) e = cudaMemsetAsync(w.maxcnt, 0, sizeof(int) * 2 * P.B, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "memset");
+    e = launch_build_impl(w, pos, types, h->d_rk, P.bsum, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "neighbour build launch");
+    if (P.Nr > 0) h->launches += kBuildLaunches;
+    return D3_OK;
+}
+
+// Make the plan match the geometry; on a new geometry run the build once
+// synchronously and grow image and list capacities until nothing overflows.
+d3_status ensure_plan(d3_handle* h, int32_t B, const int64_t* offsets, const double* pos, const int32_t* types,
+                      const double* cells, const int32_t* pbc, cudaStream_t st) {
+    Plan& P = h->plan;
+    if (same_geometry(P, B, offsets, cells, pbc) && P.sized) return D3_OK;
+    if (!same_geometry(P, B, offsets, cells, pbc)) {
+        P.valid = false;
+        P.sized = false;
+        P.B = B;
+        P.offsets.assign(offsets, offsets + B + 1);
+        P.cells.assign(cells, cells + 9 * (size_t)B);
+        P.pbc.assign(pbc, pbc + 3 * (size_t)B);
+        P.Nr = offsets[B];
+        std::vector<double> gest;
+        d3_status s = plan_geometry(h, P, B, offsets, cells, pbc, gest);
+        if (s != D3_OK) return s;
+        double g = 64.0;
+        for (double x : gest) g += 1.15 * x + 8.0;
+        if (g > 2.0e9) return fail(h, D3_ERR_ARG, "too many periodic images");
+        P.ghost_cap = (int)g;
+        s = plan_alloc(h, P);
+        if (s != D3_OK) return s;
+        P.valid = true;
+    }
+    for (int attempt = 0; attempt < 4; ++attempt) {
+        cudaError_t e = cudaMemsetAsync(h->d_status, 0, sizeof(int), st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "status reset");
+        d3_status s = enqueue_build(h, P, pos, types, st);
+        if (s != D3_OK) return s;
+        int gcount = 0, status = 0;
+        std::vector<int> mx(2 * (size_t)std::max(B, 1), 0);
+        e = cudaMemcpyAsync(&gcount, P.w.ghost_count, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && B > 0) e = cudaMemcpyAsync(mx.data(), P.w.maxcnt, sizeof(int) * 2 * B, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&status, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "sizing pass");
+        if (status & ST_NONFINITE) return fail(h, D3_ERR_NONFINITE, "non-finite coordinate");
+        if (status & ST_TYPE) return fail(h, D3_ERR_TYPE, "atom type out of range");
+        bool grow = false;
+        if (gcount > P.ghost_cap) {
+            P.ghost_cap = (int)std::min<double>(2.0e9, gcount * 1.1 + 64);
+            grow = true;
+        }
+        for (int s2 = 0; s2 < B; ++s2) {
+            StructGeo& G = P.geo[s2];
+            if (mx[2 * s2] > G.cap_disp) { G.cap_disp = round_cap(mx[2 * s2] * 1.1 + 16); grow = true; }
+            if (mx[2 * s2 + 1] > G.cap_cn) { G.cap_cn = round_cap(mx[2 * s2 + 1] * 1.1 + 8); grow = true; }
+        }
+        if (!grow) {
+            P.sized = true;
+            return D3_OK;
+        }
+        s = plan_alloc(h, P);
+        if (s != D3_OK) return s;
+    }
+    return fail(h, D3_ERR_CAPACITY, "workspace sizing did not converge");
+}
+
+d3_status check_batch_args(d3_handle* h, int32_t B, const int64_t* offsets, const double* pos, const int32_t* types,
+                           const double* cells, const int32_t* pbc) {
+    if (!h) return D3_ERR_ARG;
+    if (B < 0 || !offsets || (B > 0 && (!cells || !pbc))) return fail(h, D3_ERR_ARG, "bad batch description");
+    if (offsets[0] != 0) return fail(h, D3_ERR_ARG, "offsets[0] must be 0");
+    for (int s = 0; s < B; ++s)
+        if (offsets[s + 1] < offsets[s]) return fail(h, D3_ERR_ARG, "offsets must be non-decreasing");
+    if (offsets[B] > ((int64_t)1 << 27)) return fail(h, D3_ERR_ARG, "too many atoms (max 2^27)");
+    if (offsets[B] > 0 && (!pos || !types)) return fail(h, D3_ERR_ARG, "NULL positions or types");
+    return D3_OK;
+}
+
+d3_status forward(d3_handle* h, int32_t B, const int64_t* offsets, const double* pos, const int32_t* types,
+                  const double* cells, const int32_t* pbc, double* E, double* F, double* W, double* e_atom,
+                  double* cn, cudaStream_t st) {
+    d3_status s = check_batch_args(h, B, offsets, pos, types, cells, pbc);
+    if (s != D3_OK) return s;
+    if (B > 0 && (!E || !W)) return fail(h, D3_ERR_ARG, "NULL E or W");
+    if (offsets[B] > 0 && !F) return fail(h, D3_ERR_ARG, "NULL F");
+    h->last_stream = st;
+    if (B == 0) return D3_OK;
+    s = ensure_plan(h, B, offsets, pos, types, cells, pbc, st);
+    if (s != D3_OK) return s;
+    Plan& P = h->plan;
+    std::vector<cudaEvent_t> ev;
+    if (h->prof_on) {
+        ev = take_events(h, 7);
+        if (ev.size() == 7) cudaEventRecord(ev[0], st);
+    }
+    s = enqueue_build(h, P, pos, types, st);
+    if (s != D3_OK) return s;
+    const Consts c = make_consts(h);
+    const bool mixed = h->prm.precision == D3_MIXED;
+    Tabs tb;
+    tb.c6 = mixed ? (const void*)h->d_c6f : (const void*)h->d_c6d;
+    tb.pair = mixed ? (const void*)h->d_pairf : (const void*)h->d_paird;
+    tb.cnref = h->d_cnref;
+    tb.nref = h->d_nref;
+    tb.rcpair = h->d_rcpair;
+    cudaError_t e = launch_forward(P.w, c, mixed, tb, E, F, W, e_atom, cn, B, st,
+                                   ev.size() == 7 ? ev.data() + 1 : nullptr);
+    if (e != cudaSuccess) return cuda_fail(h, e, "forward launch");
+    h->launches += (P.Nr > 0 ? kForwardLaunches - 1 : 1);
+    if (ev.size() == 7) h->ev_pending.push_back(ev);
+    else for (cudaEvent_t x : ev) h->ev_pool.push_back(x);
+    return D3_OK;
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+const char* d3_version(void) { return "d3gb 0.1 (sm_103a)"; }
+
+d3_status d3_create(const d3_params* params, const d3_tables* tables, d3_handle** out) {
+    if (!out) return D3_ERR_ARG;
+    *out = nullptr;
+    if (!params || !tables) return D3_ERR_ARG;
+    const d3_tables& t = *tables;
+    if (t.ntypes < 1 || t.ntypes > kMaxTypes || t.max_ref < 1 || t.max_ref > kMaxRef || !t.nref || !t.cn_ref ||
+        !t.c6_ref || !t.rcov_bohr || !t.sqrtq)
+        return D3_ERR_ARG;
+    const d3_params& p = *params;
+    if (!(p.rc_disp_A > 0) || !(p.rc_cn_A > 0) || !(p.k1 > 0) || !(p.k3 > 0) || p.skin_A < 0 ||
+        (p.precision != D3_FP64 && p.precision != D3_MIXED) || !std::isfinite(p.s6) || !std::isfinite(p.s8) ||
+        !std::isfinite(p.a1) || !std::isfinite(p.a2_bohr))
+        return D3_ERR_ARG;
+    const int T = t.ntypes, R = t.max_ref;
+    for (int a = 0; a < T; ++a) {
+        if (t.nref[a] < 1 || t.nref[a] > R) return D3_ERR_ARG;
+        if (!(t.rcov_bohr[a] > 0) || !(t.sqrtq[a] > 0)) return D3_ERR_ARG;
+    }
+    for (int a = 0; a < T; ++a)
+        for (int b = 0; b < T; ++b)
+            for (int i = 0; i < R; ++i)
+                for (int j = 0; j < R; ++j) {
+                    const double x = t.c6_ref[((a * T + b) * R + i) * R + j];
+                    const double y = t.c6_ref[((b * T + a) * R + j) * R + i];
+                    if (!std::isfinite(x) || x != y) return D3_ERR_ARG;
+                }
+    d3_handle* h = new d3_handle();
+    h->prm = p;
+    h->T = T;
+    h->R = R;
+    h->RP = (R + 3) / 4 * 4;
+    h->nref.assign(t.nref, t.nref + T);
+    h->cnref.assign(t.cn_ref, t.cn_ref + T * R);
+    h->c6.assign(t.c6_ref, t.c6_ref + (size_t)T * T * R * R);
+    h->rcov.assign(t.rcov_bohr, t.rcov_bohr + T);
+    h->sqrtq.assign(t.sqrtq, t.sqrtq + T);
+    // padding entries (a >= nref) of C6 are never weighted, zero them for safety
+    for (int a = 0; a < T; ++a)
+        for (int b = 0; b < T; ++b)
+            for (int i = 0; i < R; ++i)
+                for (int j = 0; j < R; ++j)
+                    if (i >= h->nref[a] || j >= h->nref[b]) h->c6[((a * T + b) * R + i) * R + j] = 0.0;
+    std::vector<float> c6f(h->c6.begin(), h->c6.end());
+    std::vector<double> rk(T);
+    for (int a = 0; a < T; ++a) rk[a] = p.k2 * h->rcov[a];
+    cudaError_t e = cudaSuccess;
+    DevBuf& m = h->tabmem;
+    if (e == cudaSuccess) e = m.alloc(&h->d_nref, T);
+    if (e == cudaSuccess) e = m.alloc(&h->d_cnref, T * R);
+    if (e == cudaSuccess) e = m.alloc(&h->d_c6f, h->c6.size());
+    if (e == cudaSuccess) e = m.alloc(&h->d_c6d, h->c6.size());
+    if (e == cudaSuccess) e = m.alloc(&h->d_pairf, T * T);
+    if (e == cudaSuccess) e = m.alloc(&h->d_paird, T * T);
+    if (e == cudaSuccess) e = m.alloc(&h->d_pairb, T * T);
+    if (e == cudaSuccess) e = m.alloc(&h->d_rcpair, T * T);
+    if (e == cudaSuccess) e = m.alloc(&h->d_rk, T);
+    if (e == cudaSuccess) e = m.alloc(&h->d_status, 1);
+    if (e == cudaSuccess) e = cudaMemcpy(h->d_nref, h->nref.data(), T * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(h->d_cnref, h->cnref.data(), T * R * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(h->d_c6f, c6f.data(), c6f.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(h->d_c6d, h->c6.data(), h->c6.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(h->d_rk, rk.data(), T * sizeof(double), cudaMemcpyHostToDevice);
+    std::vector<float4> rcp(T * T);
+    for (int a2 = 0; a2 < T; ++a2)
+        for (int b2 = 0; b2 < T; ++b2) {
+            const double rc = p.k2 * (h->rcov[a2] + h->rcov[b2]);
+            const float rh = (float)rc, rl = (float)(rc - (double)rh);
+            const double rc2 = rc * rc;
+            const float qh = (float)rc2, ql = (float)(rc2 - (double)qh);
+            rcp[a2 * T + b2] = make_float4(rh, rl, qh, ql);
+        }
+    if (e == cudaSuccess) e = cudaMemcpy(h->d_rcpair, rcp.data(), rcp.size() * sizeof(float4), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(h->d_status, 0, sizeof(int));
+    if (e != cudaSuccess) {
+        h->tabmem.release();
+        delete h;
+        return D3_ERR_CUDA;
+    }
+    if (upload_pair_table(h) != D3_OK) {
+        h->tabmem.release();
+        delete h;
+        return D3_ERR_CUDA;
+    }
+    *out = h;
+    return D3_OK;
+}
+
+void d3_destroy(d3_handle* h) {
+    if (!h) return;
+    cudaDeviceSynchronize();
+    for (auto& v : h->ev_pending)
+        for (cudaEvent_t e : v) cudaEventDestroy(e);
+    for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+    h->plan.mem.release();
+    h->stage.release();
+    h->tabmem.release();
+    delete h;
+}
+
+d3_status d3_set_damping(d3_handle* h, double s6, double s8, double a1, double a2_bohr) {
+    if (!h) return D3_ERR_ARG;
+    if (!std::isfinite(s6) || !std::isfinite(s8) || !std::isfinite(a1) || !std::isfinite(a2_bohr))
+        return fail(h, D3_ERR_ARG, "non-finite damping parameter");
+    if (h->last_stream) cudaStreamSynchronize(h->last_stream);
+    h->prm.s6 = s6;
+    h->prm.s8 = s8;
+    h->prm.a1 = a1;
+    h->prm.a2_bohr = a2_bohr;
+    return upload_pair_table(h);
+}
+
+d3_status d3_build_neighbors(d3_handle* h, int32_t B, const int64_t* offsets, const double* pos,
+                             const int32_t* types, const double* cells, const int32_t* pbc, void* stream) {
+    d3_status s = check_batch_args(h, B, offsets, pos, types, cells, pbc);
+    if (s != D3_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    h->last_stream = st;
+    if (B == 0) return D3_OK;
+    s = ensure_plan(h, B, offsets, pos, types, cells, pbc, st);
+    if (s != D3_OK) return s;
+    s = enqueue_build(h, h->plan, pos, types, st);
+    if (s != D3_OK) return s;
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "build");
+    return d3_sync_status(h);
+}
+
+d3_status d3_compute_batch_ex(d3_handle* h, int32_t B, const int64_t* offsets, const double* pos,
+                              const int32_t* types, const double* cells, const int32_t* pbc, double* E, double* F,
+                              double* W, double* e_atom, double* cn, void* stream) {
+    return forward(h, B, offsets, pos, types, cells, pbc, E, F, W, e_atom, cn, (cudaStream_t)stream);
+}
+
+d3_status d3_compute_batch(d3_handle* h, int32_t B, const int64_t* offsets, const double* pos,
+                           const int32_t* types, const double* cells, const int32_t* pbc, double* E, double* F,
+                           double* W, void* stream) {
+    return forward(h, B, offsets, pos, types, cells, pbc, E, F, W, nullptr, nullptr, (cudaStream_t)stream);
+}
+
+d3_status d3_compute(d3_handle* h, const double* pos, const int32_t* types, int64_t n, const double* cell,
+                     const int32_t* pbc, double* E, double* F, double* W, void* stream) {
+    if (!h) return D3_ERR_ARG;
+    if (n < 0 || !cell || !pbc) return fail(h, D3_ERR_ARG, "bad structure description");
+    const int64_t off[2] = {0, n};
+    return forward(h, 1, off, pos, types, cell, pbc, E, F, W, nullptr, nullptr, (cudaStream_t)stream);
+}
+
+d3_status d3_compute_batch_host(d3_handle* h, int32_t B, const int64_t* offsets, const double* pos,
+                                const int32_t* types, const double* cells, const int32_t* pbc, double* E,
+                                double* F, double* W, void* stream) {
+    d3_status s = check_batch_args(h, B, offsets, pos, types, cells, pbc);
+    if (s != D3_OK) return s;
+    if (B == 0) return D3_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t N = (size_t)offsets[B];
+    if (N > h->stage_atoms || (size_t)B > h->stage_structs) {
+        h->stage.release();
+        h->stage_atoms = std::max(N, h->stage_atoms);
+        h->stage_structs = std::max((size_t)B, h->stage_structs);
+        cudaError_t e = h->stage.alloc(&h->s_pos, 3 * h->stage_atoms);
+        if (e == cudaSuccess) e = h->stage.alloc(&h->s_F, 3 * h->stage_atoms);
+        if (e == cudaSuccess) e = h->stage.alloc(&h->s_types, h->stage_atoms);
+        if (e == cudaSuccess) e = h->stage.alloc(&h->s_E, h->stage_structs);
+        if (e == cudaSuccess) e = h->stage.alloc(&h->s_W, 9 * h->stage_structs);
+        if (e != cudaSuccess) {
+            h->stage.release();
+            h->stage_atoms = h->stage_structs = 0;
+            return cuda_fail(h, e, "staging allocation");
+        }
+    }
+    cudaError_t e = cudaMemcpyAsync(h->s_pos, pos, 3 * N * sizeof(double), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->s_types, types, N * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "input copy");
+    s = forward(h, B, offsets, h->s_pos, h->s_types, cells, pbc, h->s_E, h->s_F, h->s_W, nullptr, nullptr, st);
+    if (s != D3_OK) return s;
+    e = cudaMemcpyAsync(E, h->s_E, B * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(F, h->s_F, 3 * N * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(W, h->s_W, 9 * (size_t)B * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "output copy");
+    return d3_sync_status(h);
+}
+
+d3_status d3_backward(d3_handle* h, int32_t B, const int64_t* offsets, const double* pos, const int32_t* types,
+                      const double* cells, const int32_t* pbc, const double* dLdE, const double* dLdF,
+                      double* dLdparams, double* dLdpos, void* stream) {
+    d3_status s = check_batch_args(h, B, offsets, pos, types, cells, pbc);
+    if (s != D3_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    h->last_stream = st;
+    if (B > 0 && !dLdE) return fail(h, D3_ERR_ARG, "NULL dLdE");
+    if (offsets[B] > 0 && !dLdF) return fail(h, D3_ERR_ARG, "NULL dLdF");
+    if (B == 0) {
+        if (dLdparams) {
+            cudaError_t e = cudaMemsetAsync(dLdparams, 0, 4 * sizeof(double), st);
+            if (e != cudaSuccess) return cuda_fail(h, e, "memset");
+        }
+        return D3_OK;
+    }
+    s = ensure_plan(h, B, offsets, pos, types, cells, pbc, st);
+    if (s != D3_OK) return s;
+    Plan& P = h->plan;
+    s = enqueue_build(h, P, pos, types, st);
+    if (s != D3_OK) return s;
+    const int64_t need = backward_scratch_doubles(P.w, B);
+    if (need > P.bwd_scratch_n) {
+        double* p = nullptr;
+        cudaError_t e = P.mem.alloc(&p, (size_t)need);
+        if (e != cudaSuccess) return cuda_fail(h, e, "backward scratch");
+        P.bwd_scratch = p;
+        P.bwd_scratch_n = need;
+    }
+    Consts c = make_consts(h);
+    cudaError_t e = launch_backward(P.w, c, h->d_c6d, h->d_pairb, h->d_cnref, h->d_nref, dLdE, dLdF, dLdparams,
+                                    dLdpos, P.bwd_scratch, B, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "backward launch");
+    return D3_OK;
+}
+
+d3_status d3_sync_status(d3_handle* h) {
+    if (!h) return D3_ERR_ARG;
+    cudaError_t e = cudaStreamSynchronize(h->last_stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "synchronize");
+    int st = 0;
+    e = cudaMemcpy(&st, h->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(h->d_status, 0, sizeof(int));
+    if (e != cudaSuccess) return cuda_fail(h, e, "status read");
+    if (st & ST_NONFINITE) return fail(h, D3_ERR_NONFINITE, "non-finite coordinate");
+    if (st & ST_TYPE) return fail(h, D3_ERR_TYPE, "atom type out of range");
+    if (st & (ST_GHOST_CAP | ST_LIST_CAP)) {
+        h->plan.sized = false;  // the next call re-measures and regrows
+        return fail(h, D3_ERR_CAPACITY, "neighbour or image capacity exceeded; buffers will be regrown");
+    }
+    h->err.clear();
+    return D3_OK;
+}
+
+const char* d3_last_error(const d3_handle* h) { return h ? h->err.c_str() : "NULL handle"; }
+
+d3_status d3_profile_enable(d3_handle* h, int32_t on) {
+    if (!h) return D3_ERR_ARG;
+    h->prof_on = on != 0;
+    return D3_OK;
+}
+
+d3_status d3_profile_read(d3_handle* h, double* ms, int64_t* calls, int64_t* launches) {
+    if (!h) return D3_ERR_ARG;
+    for (auto& v : h->ev_pending) {
+        cudaError_t e = cudaEventSynchronize(v[6]);
+        if (e != cudaSuccess) return cuda_fail(h, e, "profile event");
+        for (int k = 0; k < 6; ++k) {
+            float t = 0.f;
+            if (cudaEventElapsedTime(&t, v[k], v[k + 1]) == cudaSuccess) {
+                h->prof_ms[k] += t;
+                h->prof_calls[k] += 1;
+            }
+        }
+        for (cudaEvent_t x : v) h->ev_pool.push_back(x);
+    }
+    h->ev_pending.clear();
+    for (int k = 0; k < 6; ++k) {
+        if (ms) ms[k] = h->prof_ms[k];
+        if (calls) calls[k] = h->prof_calls[k];
+    }
+    if (launches) *launches = h->launches;
+    return D3_OK;
+}
+
+d3_status d3_profile_reset(d3_handle* h) {
+    if (!h) return D3_ERR_ARG;
+    d3_status s = d3_profile_read(h, nullptr, nullptr, nullptr);
+    for (int k = 0; k < 6; ++k) {
+        h->prof_ms[k] = 0;
+        h->prof_calls[k] = 0;
+    }
+    h->launches = 0;
+    return s;
+}
+
+}  // extern "C"

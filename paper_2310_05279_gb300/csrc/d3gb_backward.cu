@@ -1,0 +1,353 @@
+// d3gb_backward.cu -- hand-written backward of (E, F) for damping refits.
+//
+// For a loss L(E, F) with upstream gradients gE = dL/dE (per structure) and
+// gF = dL/dF (per atom):
+//   dL/dtheta = sum_s gE_s dE_s/dtheta + sum_i gF_i . dF_i/dtheta
+//             = sum_s gE_s dE_s/dtheta - d/dtheta (d/dt E(x + t gF))
+//   dL/dx     = -gE F + J^T gF,  J = dF/dx = -Hessian (symmetric), so J^T gF = d/dt F(x + t gF).
+// Both second-order terms are directional derivatives along u = gF.  They are
+// obtained by running the whole evaluation (Eq. 4 coordination numbers, Eq. 3
+// weights, Eq. 2 pair terms with their analytic derivatives in s6, s8, a1, a2,
+// and the coordination-number chain rule) once in dual numbers (value,
+// derivative along u), in FP64.  The coordination numbers are recomputed and
+// nothing is stored per pair.
+#include "d3gb_internal.cuh"
+
+namespace d3gb {
+
+namespace {
+
+struct Dual {
+    double v, t;
+};
+__device__ __forceinline__ Dual dd(double v, double t = 0.0) { return Dual{v, t}; }
+__device__ __forceinline__ Dual operator+(Dual a, Dual b) { return Dual{a.v + b.v, a.t + b.t}; }
+__device__ __forceinline__ Dual operator-(Dual a, Dual b) { return Dual{a.v - b.v, a.t - b.t}; }
+__device__ __forceinline__ Dual operator-(Dual a) { return Dual{-a.v, -a.t}; }
+__device__ __forceinline__ Dual operator*(Dual a, Dual b) { return Dual{a.v * b.v, a.v * b.t + a.t * b.v}; }
+__device__ __forceinline__ Dual operator*(double s, Dual a) { return Dual{s * a.v, s * a.t}; }
+__device__ __forceinline__ Dual operator+(Dual a, double s) { return Dual{a.v + s, a.t}; }
+__device__ __forceinline__ Dual& operator+=(Dual& a, Dual b) {
+    a.v += b.v;
+    a.t += b.t;
+    return a;
+}
+__device__ __forceinline__ Dual inv(Dual a) {
+    const double r = 1.0 / a.v;
+    return Dual{r, -a.t * r * r};
+}
+__device__ __forceinline__ Dual dexp(Dual a) {
+    const double e = exp(a.v);
+    return Dual{e, a.t * e};
+}
+__device__ __forceinline__ Dual dsqrt(Dual a) {
+    const double s = sqrt(a.v);
+    return Dual{s, 0.5 * a.t / s};
+}
+
+// per-atom dual arrays carved from one scratch block
+struct BW {
+    Dual* n;      // [Nr]
+    Dual* W;      // [Nr][R]
+    Dual* dW;     // [Nr][R]
+    Dual* v;      // [Nr][T][R]
+    Dual* dEdn;   // [Nr]
+    Dual* F;      // [Nr][3]
+    Dual* th;     // [Nr][4] dE_i/d(s6, s8, a1, a2), half pair sums
+    double* xd;   // [(Nr + ghost_cap) * 3] tangent positions (bohr)
+    double* sth;  // [B][8] per-structure dE/dtheta (value, tangent)
+};
+
+__host__ __device__ inline BW carve(double* s, int64_t Nr, int64_t Ng, int T, int R, int B) {
+    BW b;
+    Dual* d = reinterpret_cast<Dual*>(s);
+    b.n = d;
+    d += Nr;
+    b.W = d;
+    d += Nr * R;
+    b.dW = d;
+    d += Nr * R;
+    b.v = d;
+    d += Nr * T * R;
+    b.dEdn = d;
+    d += Nr;
+    b.F = d;
+    d += 3 * Nr;
+    b.th = d;
+    d += 4 * Nr;
+    double* x = reinterpret_cast<double*>(d);
+    b.xd = x;
+    x += 3 * (Nr + Ng);
+    b.sth = x;
+    return b;
+}
+
+struct BConsts {
+    double rc_disp2, rc_cn2, k1, k3, s6, s8;
+    int T, R;
+};
+
+// tangent positions: x(t) = x + t * gF / bohr for real atoms, images follow their source
+__global__ void kb_xdot(Work w, BW b, const double* __restrict__ gF, int64_t nt) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nt || q >= w.Nr + w.start_ghost[w.ncells]) return;
+    const int src = __float_as_int(w.hi[q].w) >> 4;
+    const int i = w.perm[src];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) b.xd[3 * q + a] = gF[3 * (int64_t)i + a] * (1.0 / kBohrA);
+}
+
+__device__ __forceinline__ void ddist(const Work& w, const BW& b, int64_t p, int64_t q, Dual (&d)[3], Dual& r2) {
+    const dbl4 x = w.pos64[p], y = w.pos64[q];
+    d[0] = Dual{y.x - x.x, b.xd[3 * q] - b.xd[3 * p]};
+    d[1] = Dual{y.y - x.y, b.xd[3 * q + 1] - b.xd[3 * p + 1]};
+    d[2] = Dual{y.z - x.z, b.xd[3 * q + 2] - b.xd[3 * p + 2]};
+    r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+}
+
+__global__ void kb_cn(Work w, BW b, BConsts c) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= w.Nr) return;
+    const StructGeo& G = w.geo[w.sid[p]];
+    const ListView LV{w.nbr_cn + list_row(G.list_base_cn, p - G.atom_base, G.cap_cn)};
+    const int cnt = w.cnt_cn[p];
+    const double rki = w.pos64[p].w;
+    Dual n = dd(0.0);
+    LV.for_each(0, cnt, [&](int q) {
+        Dual d[3], r2;
+        ddist(w, b, p, q, d, r2);
+        if (!(r2.v < c.rc_cn2)) return;
+        const Dual rinv = inv(dsqrt(r2));
+        const double rc = rki + w.pos64[q].w;
+        const Dual t = dexp(-c.k1 * (rc * rinv + (-1.0)));
+        n += inv(t + 1.0);
+    });
+    b.n[p] = n;
+}
+
+template <int R>
+__global__ void kb_weights(Work w, BW b, BConsts c, const double* __restrict__ cnref, const int* __restrict__ nref,
+                           const double* __restrict__ c6) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= w.Nr) return;
+    const int t = __float_as_int(w.hi[p].w) & 15;
+    const Dual n = b.n[p];
+    const int nr = nref[t];
+    Dual z[R], ex[R], L[R];
+    double emax = -1e300;
+#pragma unroll
+    for (int a = 0; a < R; ++a) {
+        z[a] = n + (-cnref[t * R + a]);
+        ex[a] = -c.k3 * (z[a] * z[a]);
+        if (a < nr && ex[a].v > emax) emax = ex[a].v;
+    }
+    Dual sum = dd(0.0);
+#pragma unroll
+    for (int a = 0; a < R; ++a) {
+        L[a] = a < nr ? dexp(ex[a] + (-emax)) : dd(0.0);
+        sum += L[a];
+    }
+    const Dual is = inv(sum);
+    Dual gbar = dd(0.0);
+#pragma unroll
+    for (int a = 0; a < R; ++a) {
+        L[a] = L[a] * is;
+        gbar += L[a] * (-2.0 * c.k3 * z[a]);
+    }
+#pragma unroll
+    for (int a = 0; a < R; ++a) {
+        b.W[p * R + a] = L[a];
+        b.dW[p * R + a] = L[a] * ((-2.0 * c.k3 * z[a]) - gbar);
+    }
+    for (int u = 0; u < c.T; ++u) {
+        const double* cu = c6 + ((size_t)(u * c.T + t) * R) * R;
+#pragma unroll
+        for (int a = 0; a < R; ++a) {
+            Dual s = dd(0.0);
+#pragma unroll
+            for (int bb = 0; bb < R; ++bb) s += cu[a * R + bb] * L[bb];
+            b.v[(p * c.T + u) * R + a] = s;
+        }
+    }
+}
+
+// pairb[ti*T + tj] = (R0, R, R0^2, 0) in bohr
+template <int R>
+__global__ void kb_disp(Work w, BW b, BConsts c, const dbl4* __restrict__ pairb) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= w.Nr) return;
+    const int ti = __float_as_int(w.hi[p].w) & 15;
+    Dual Wi[R], dWi[R];
+#pragma unroll
+    for (int a = 0; a < R; ++a) {
+        Wi[a] = b.W[p * R + a];
+        dWi[a] = b.dW[p * R + a];
+    }
+    const StructGeo& G = w.geo[w.sid[p]];
+    const ListView LV{w.nbr_disp + list_row(G.list_base_disp, p - G.atom_base, G.cap_disp)};
+    const int cnt = w.cnt_disp[p];
+    Dual dn = dd(0.0), F[3] = {dd(0.0), dd(0.0), dd(0.0)}, th[4] = {dd(0.0), dd(0.0), dd(0.0), dd(0.0)};
+    LV.for_each(0, cnt, [&](int q) {
+        Dual d[3], r2;
+        ddist(w, b, p, q, d, r2);
+        if (!(r2.v < c.rc_disp2)) return;
+        const int tsq = __float_as_int(w.hi[q].w);
+        const int src = tsq >> 4;
+        const dbl4 pb = pairb[ti * c.T + (tsq & 15)];
+        const double R0 = pb.x, Rd = pb.y, R0sq = pb.z;
+        const double R2 = Rd * Rd, R4 = R2 * R2, R6 = R4 * R2, R8 = R4 * R4;
+        Dual C6 = dd(0.0), dC6 = dd(0.0);
+#pragma unroll
+        for (int a = 0; a < R; ++a) {
+            const Dual vq = b.v[((int64_t)src * c.T + ti) * R + a];
+            C6 += Wi[a] * vq;
+            dC6 += dWi[a] * vq;
+        }
+        const Dual r4 = r2 * r2, r6 = r4 * r2, r8 = r4 * r4;
+        const Dual i6 = inv(r6 + R6), i8 = inv(r8 + R8);
+        const Dual t6 = c.s6 * i6, t8 = (c.s8 * R0sq) * i8;
+        const Dual g = t6 + t8;
+        dn += -(g * dC6);
+        const Dual fc = C6 * (6.0 * (r4 * (t6 * i6)) + 8.0 * (r6 * (t8 * i8)));
+#pragma unroll
+        for (int a = 0; a < 3; ++a) F[a] += fc * d[a];
+        // derivatives of this ordered instance's energy -C6 g (halved at the end)
+        th[0] += -(C6 * i6);
+        th[1] += -(R0sq * (C6 * i8));
+        const Dual dR = C6 * ((c.s6 * 6.0 * R4 * Rd) * (i6 * i6) + (c.s8 * R0sq * 8.0 * R6 * Rd) * (i8 * i8));
+        th[2] += R0 * dR;
+        th[3] += dR;
+    });
+    b.dEdn[p] = dn;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) b.F[3 * p + a] = F[a];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) b.th[4 * p + m] = 0.5 * th[m];
+}
+
+__global__ void kb_chain(Work w, BW b, BConsts c, const double* __restrict__ gE, double* __restrict__ dLdx) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= w.Nr) return;
+    const int s = w.sid[p];
+    const StructGeo& G = w.geo[s];
+    const ListView LV{w.nbr_cn + list_row(G.list_base_cn, p - G.atom_base, G.cap_cn)};
+    const int cnt = w.cnt_cn[p];
+    const double rki = w.pos64[p].w;
+    const Dual dni = b.dEdn[p];
+    Dual F[3] = {b.F[3 * p], b.F[3 * p + 1], b.F[3 * p + 2]};
+    LV.for_each(0, cnt, [&](int q) {
+        Dual d[3], r2;
+        ddist(w, b, p, q, d, r2);
+        if (!(r2.v < c.rc_cn2)) return;
+        const int src = __float_as_int(w.hi[q].w) >> 4;
+        const Dual rinv = inv(dsqrt(r2));
+        const double rc = rki + w.pos64[q].w;
+        const Dual t = dexp(-c.k1 * (rc * rinv + (-1.0)));
+        const Dual f = inv(t + 1.0);
+        const Dual dfdr = (-c.k1 * rc) * (rinv * rinv * t * f * f);
+        const Dual coef = (dni + b.dEdn[src]) * dfdr * rinv;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) F[a] += coef * d[a];
+    });
+    if (dLdx) {
+        const double u = kHartreeEV / kBohrA;
+        const double ge = gE[s];
+        const int i = w.perm[p];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) dLdx[3 * (int64_t)i + a] = (-ge * F[a].v + F[a].t) * u;
+    }
+}
+
+// per-structure sums of dE/dtheta (value and tangent), fixed order
+__global__ void __launch_bounds__(256) kb_struct_sum(Work w, BW b) {
+    const int s = blockIdx.x;
+    const StructGeo& G = w.geo[s];
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int64_t k = threadIdx.x; k < G.natoms; k += blockDim.x) {
+        const int64_t p = G.atom_base + k;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            acc[m] += b.th[4 * p + m].v;
+            acc[4 + m] += b.th[4 * p + m].t;
+        }
+    }
+    __shared__ double red[8][256];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) red[m][threadIdx.x] = acc[m];
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o)
+#pragma unroll
+            for (int m = 0; m < 8; ++m) red[m][threadIdx.x] += red[m][threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x < 8) b.sth[8 * s + threadIdx.x] = red[threadIdx.x][0];
+}
+
+// dL/dtheta = sum_s gE_s dE_s/dtheta - d/dtheta(dE/dt), in eV per unit parameter
+__global__ void __launch_bounds__(256) kb_param_grad(BW b, int B, const double* __restrict__ gE, double* __restrict__ out) {
+    double acc[4] = {0, 0, 0, 0};
+    for (int s = threadIdx.x; s < B; s += blockDim.x) {
+#pragma unroll
+        for (int m = 0; m < 4; ++m) acc[m] += gE[s] * b.sth[8 * s + m] - b.sth[8 * s + 4 + m];
+    }
+    __shared__ double red[4][256];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) red[m][threadIdx.x] = acc[m];
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o)
+#pragma unroll
+            for (int m = 0; m < 4; ++m) red[m][threadIdx.x] += red[m][threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x < 4) out[threadIdx.x] = red[threadIdx.x][0] * kHartreeEV;
+}
+
+inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+template <int R>
+cudaError_t backward_impl(const Work& w, const Consts& cc, const double* c6d, const dbl4* pairb, const double* cnref,
+                          const int* nref, const double* gE, const double* gF, double* dLdp, double* dLdx,
+                          double* scratch, int B, cudaStream_t st) {
+    BW b = carve(scratch, w.Nr, w.ghost_cap, w.T, R, B);
+    BConsts c{cc.rc_disp2, cc.rc_cn2, cc.k1, cc.k3, cc.s6, cc.s8, cc.T, R};
+    const int TB = 128;
+    if (w.Nr > 0) {
+        // tangent positions for real atoms and every image actually built
+        kb_xdot<<<nblk(w.Nr + w.ghost_cap, TB), TB, 0, st>>>(w, b, gF, w.Nr + w.ghost_cap);
+        kb_cn<<<nblk(w.Nr, TB), TB, 0, st>>>(w, b, c);
+        kb_weights<R><<<nblk(w.Nr, TB), TB, 0, st>>>(w, b, c, cnref, nref, c6d);
+        kb_disp<R><<<nblk(w.Nr, TB), TB, 0, st>>>(w, b, c, pairb);
+        kb_chain<<<nblk(w.Nr, TB), TB, 0, st>>>(w, b, c, gE, dLdx);
+    }
+    kb_struct_sum<<<B, 256, 0, st>>>(w, b);
+    if (dLdp) kb_param_grad<<<1, 256, 0, st>>>(b, B, gE, dLdp);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int64_t backward_scratch_doubles(const Work& w, int B) {
+    const int64_t Nr = w.Nr, Ng = w.ghost_cap;
+    const int64_t duals = Nr * (1 + 2 * (int64_t)w.R + (int64_t)w.T * w.R + 1 + 3 + 4);
+    return 2 * duals + 3 * (Nr + Ng) + 8 * (int64_t)B + 64;
+}
+
+cudaError_t launch_backward(const Work& w, const Consts& c, const double* c6d, const dbl4* pairb,
+                            const double* cnref, const int* nref, const double* dLdE, const double* dLdF,
+                            double* dLdp, double* dLdx, double* scratch, int B, cudaStream_t st) {
+#define D3_BWD(RR) return backward_impl<RR>(w, c, c6d, pairb, cnref, nref, dLdE, dLdF, dLdp, dLdx, scratch, B, st)
+    switch (c.R) {
+        case 1: D3_BWD(1);
+        case 2: D3_BWD(2);
+        case 3: D3_BWD(3);
+        case 4: D3_BWD(4);
+        case 5: D3_BWD(5);
+        case 6: D3_BWD(6);
+        default: D3_BWD(7);
+    }
+#undef D3_BWD
+}
+
+}  // namespace d3gb

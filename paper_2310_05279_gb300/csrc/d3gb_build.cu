@@ -1,0 +1,353 @@
+// d3gb_build.cu -- neighbour build of the D3(BJ) pipeline (cell lists).
+//
+// The sums of Eq. 2 and Eq. 4 (arXiv 2310.05279, Sec. II A) run over the
+// neighbours of each atom within R_pot and R_cn, periodic images included.
+// This file turns caller-order positions into:
+//   * wrapped positions and a cell index per atom in a fractional grid that
+//     also covers a margin of one list radius around the cell,
+//   * explicit image atoms ("ghosts") for every periodic image that falls in
+//     that margin, so the pair kernels never apply lattice translations,
+//   * a counting sort of real atoms and of image atoms by cell (stable: each
+//     cell is re-sorted by source index, so the order is deterministic),
+//   * FP64 and split-FP32 (hi + lo) positions of every atom in sorted order,
+//   * per-atom neighbour lists within the two list radii.
+// Every kernel writes only inside the capacities it is given and records an
+// overflow in the status word instead.
+#include "d3gb_internal.cuh"
+
+namespace d3gb {
+
+namespace {
+
+__device__ inline int cell_id(const StructGeo& G, const double f[3]) {
+    int c[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        double u = (f[k] - G.lo[k]) * G.fscale[k];
+        u = fmin(fmax(u, 0.0), (double)(G.ncell[k] - 1));
+        c[k] = (int)u;
+    }
+    return (int)(G.cell_base + ((int64_t)c[2] * G.ncell[1] + c[1]) * G.ncell[0] + c[0]);
+}
+
+// Slot in a shared counter for every active lane of the warp, one atomic per warp.
+__device__ inline int warp_aggregated_inc(int* ctr) {
+    unsigned mask = __activemask();
+    int lane = threadIdx.x & 31;
+    int leader = __ffs(mask) - 1;
+    int rank = __popc(mask & ((1u << lane) - 1u));
+    int base = 0;
+    if (lane == leader) base = atomicAdd(ctr, __popc(mask));
+    base = __shfl_sync(mask, base, leader);
+    return base + rank;
+}
+
+__global__ void k_bin(Work w, const double* __restrict__ pos, const int32_t* __restrict__ types) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= w.Nr) return;
+    const int s = struct_of(w.offsets, w.B, i);
+    const StructGeo& G = w.geo[s];
+    double xb[3];
+    bool fin = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        xb[a] = pos[3 * i + a] * (1.0 / kBohrA);
+        fin = fin && isfinite(xb[a]);
+    }
+    if (!fin) {
+        atomicOr(w.status, ST_NONFINITE);
+        xb[0] = xb[1] = xb[2] = 0.0;
+    }
+    const int t = types[i];
+    if (t < 0 || t >= w.T) atomicOr(w.status, ST_TYPE);
+    double f[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        f[k] = xb[0] * G.Hinv[k] + xb[1] * G.Hinv[3 + k] + xb[2] * G.Hinv[6 + k];
+        if (G.pbc[k]) {
+            f[k] -= floor(f[k]);
+            if (f[k] >= 1.0) f[k] -= 1.0;
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) w.xw[3 * i + a] = f[0] * G.H[a] + f[1] * G.H[3 + a] + f[2] * G.H[6 + a];
+    const int cid = cell_id(G, f);
+    w.cell_of[i] = cid;
+    w.slot_of[i] = atomicAdd(&w.cnt_real[cid], 1);
+
+    // periodic images that land inside the margin of the grid
+    for (int n0 = -G.img[0]; n0 <= G.img[0]; ++n0)
+        for (int n1 = -G.img[1]; n1 <= G.img[1]; ++n1)
+            for (int n2 = -G.img[2]; n2 <= G.img[2]; ++n2) {
+                if (n0 == 0 && n1 == 0 && n2 == 0) continue;
+                const double g[3] = {f[0] + n0, f[1] + n1, f[2] + n2};
+                bool keep = true;
+#pragma unroll
+                for (int k = 0; k < 3; ++k)
+                    if (G.img[k] > 0 && (g[k] < G.ext_lo[k] || g[k] >= G.ext_hi[k])) keep = false;
+                if (!keep) continue;
+                const int slot = warp_aggregated_inc(w.ghost_count);
+                if (slot >= w.ghost_cap) {
+                    atomicOr(w.status, ST_GHOST_CAP);
+                    continue;
+                }
+                const int gc = cell_id(G, g);
+                w.ghost_src[slot] = (int)i;
+                w.ghost_shift[slot] = pack_shift(n0, n1, n2);
+                w.ghost_cell[slot] = gc;
+                w.ghost_slot[slot] = atomicAdd(&w.cnt_ghost[gc], 1);
+            }
+}
+
+// ---- exclusive scan of int counts (n entries) into start[0..n], start[n] = total
+constexpr int kScanBlock = 1024;
+
+__device__ inline int block_exclusive_scan(int v, int* total) {
+    __shared__ int warp_sums[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int nw = blockDim.x >> 5;
+        int s = lane < nw ? warp_sums[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < nw) warp_sums[lane] = s;
+    }
+    __syncthreads();
+    int before = wid > 0 ? warp_sums[wid - 1] : 0;
+    *total = warp_sums[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return before + x - v;
+}
+
+__global__ void k_scan_blocks(const int* __restrict__ cnt, int* __restrict__ start, int* __restrict__ bsum,
+                              int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * kScanBlock + threadIdx.x;
+    int v = i < n ? cnt[i] : 0;
+    int tot;
+    int ex = block_exclusive_scan(v, &tot);
+    if (i < n) start[i] = ex;
+    if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_sums(int* bsum, int nb, int* start, int64_t n) {
+    int carry = 0;
+    for (int base = 0; base < nb; base += kScanBlock) {
+        int i = base + threadIdx.x;
+        int v = i < nb ? bsum[i] : 0;
+        int tot;
+        int ex = block_exclusive_scan(v, &tot);
+        if (i < nb) bsum[i] = ex + carry;
+        carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) start[n] = carry;
+}
+
+__global__ void k_scan_add(int* start, const int* __restrict__ bsum, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * kScanBlock + threadIdx.x;
+    if (i < n) start[i] += bsum[blockIdx.x];
+}
+
+// ---- scatter into cell order
+__global__ void k_scatter_real(Work w) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= w.Nr) return;
+    w.sorted_src[w.start_real[w.cell_of[i]] + w.slot_of[i]] = (int)i;
+}
+
+__global__ void k_scatter_ghost(Work w) {
+    int g = blockIdx.x * blockDim.x + threadIdx.x;
+    int ng = min(*w.ghost_count, w.ghost_cap);
+    if (g >= ng) return;
+    w.gsorted[w.start_ghost[w.ghost_cell[g]] + w.ghost_slot[g]] = g;
+}
+
+// Deterministic order inside each cell: real atoms by input index, images by
+// (source, translation).
+__global__ void k_sort_cells(Work w) {
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= w.ncells) return;
+    {
+        int b = w.start_real[c], e = w.start_real[c + 1];
+        for (int k = b + 1; k < e; ++k) {
+            int key = w.sorted_src[k];
+            int m = k - 1;
+            while (m >= b && w.sorted_src[m] > key) {
+                w.sorted_src[m + 1] = w.sorted_src[m];
+                --m;
+            }
+            w.sorted_src[m + 1] = key;
+        }
+    }
+    {
+        int b = w.start_ghost[c], e = w.start_ghost[c + 1];
+        for (int k = b + 1; k < e; ++k) {
+            int g = w.gsorted[k];
+            int64_t key = ((int64_t)w.ghost_src[g] << 24) | (int64_t)w.ghost_shift[g];
+            int m = k - 1;
+            while (m >= b) {
+                int h = w.gsorted[m];
+                int64_t kh = ((int64_t)w.ghost_src[h] << 24) | (int64_t)w.ghost_shift[h];
+                if (kh <= key) break;
+                w.gsorted[m + 1] = h;
+                --m;
+            }
+            w.gsorted[m + 1] = g;
+        }
+    }
+}
+
+// Split position: hi on a 2^-10 bohr grid (exact in FP32 for |x| < 2^13 bohr),
+// lo = x - hi (|lo| <= 2^-11).  Differences of hi parts are then exact in
+// FP32, so a pair vector is recovered as D + e with no rounding lost.
+__device__ inline void store_pos(Work& w, int64_t q, const double x[3], double rk, int tsrc) {
+    w.pos64[q] = dbl4_make(x[0], x[1], x[2], rk);
+    float h[3], l[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const double g = rint(x[a] * 1024.0) * (1.0 / 1024.0);
+        h[a] = (float)g;
+        l[a] = (float)(x[a] - (double)h[a]);
+    }
+    w.hi[q] = make_float4(h[0], h[1], h[2], __int_as_float(tsrc));
+    w.lo[q] = make_float4(l[0], l[1], l[2], (float)rk);
+}
+
+__global__ void k_fill_real(Work w, const int32_t* __restrict__ types, const double* __restrict__ rk_tab) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= w.Nr) return;
+    const int i = w.sorted_src[p];
+    int t = types[i];
+    if (t < 0 || t >= w.T) t = 0;
+    w.perm[p] = i;
+    w.sid[p] = struct_of(w.offsets, w.B, i);
+    w.cell_sorted[p] = w.cell_of[i];
+    w.slot_of[i] = (int)p;  // slot_of becomes the inverse permutation from here on
+    const double x[3] = {w.xw[3 * i], w.xw[3 * i + 1], w.xw[3 * i + 2]};
+    store_pos(w, p, x, rk_tab[t], t | ((int)p << 4));
+}
+
+__global__ void k_fill_ghost(Work w, const int32_t* __restrict__ types, const double* __restrict__ rk_tab) {
+    int q = blockIdx.x * blockDim.x + threadIdx.x;
+    int ng = w.start_ghost[w.ncells];
+    if (q >= ng) return;
+    const int g = w.gsorted[q];
+    const int i = w.ghost_src[g];
+    int n0, n1, n2;
+    unpack_shift(w.ghost_shift[g], n0, n1, n2);
+    const StructGeo& G = w.geo[struct_of(w.offsets, w.B, i)];
+    int t = types[i];
+    if (t < 0 || t >= w.T) t = 0;
+    double x[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) x[a] = w.xw[3 * i + a] + (n0 * G.H[a] + n1 * G.H[3 + a] + n2 * G.H[6 + a]);
+    store_pos(w, w.Nr + q, x, rk_tab[t], t | (w.slot_of[i] << 4));
+}
+
+// Per-atom lists within the two list radii (FP32 split positions; the list
+// radii carry a relative margin so every pair inside the true cutoff is listed).
+__global__ void k_build_lists(Work w) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= w.Nr) return;
+    const int s = w.sid[p];
+    const StructGeo& G = w.geo[s];
+    int rel = w.cell_sorted[p] - (int)G.cell_base;
+    const int c0 = rel % G.ncell[0];
+    rel /= G.ncell[0];
+    const int c1 = rel % G.ncell[1];
+    const int c2 = rel / G.ncell[1];
+    const float4 hp = w.hi[p];
+    const int64_t local = p - G.atom_base;
+    int* Ld = w.nbr_disp + list_row(G.list_base_disp, local, G.cap_disp);
+    int* Lc = w.nbr_cn + list_row(G.list_base_cn, local, G.cap_cn);
+    const int capd = G.cap_disp, capc = G.cap_cn;
+    int nd = 0, nc = 0;
+    const float rd2 = w.rl_disp2, rn2 = w.rl_cn2;
+    const int z0 = max(0, c2 - G.win[2]), z1 = min(G.ncell[2] - 1, c2 + G.win[2]);
+    const int y0 = max(0, c1 - G.win[1]), y1 = min(G.ncell[1] - 1, c1 + G.win[1]);
+    const int x0 = max(0, c0 - G.win[0]), x1 = min(G.ncell[0] - 1, c0 + G.win[0]);
+    for (int z = z0; z <= z1; ++z)
+        for (int y = y0; y <= y1; ++y) {
+            const int64_t row = G.cell_base + ((int64_t)z * G.ncell[1] + y) * G.ncell[0];
+            for (int pass = 0; pass < 2; ++pass) {
+                const int* st = pass == 0 ? w.start_real : w.start_ghost;
+                const int64_t off = pass == 0 ? 0 : w.Nr;
+                const int b = st[row + x0], e = st[row + x1 + 1];
+                for (int u = b; u < e; ++u) {
+                    const int64_t q = off + u;
+                    if (q == p) continue;
+                    // grid-aligned hi parts: error <= sqrt(3) 2^-10 bohr, covered by the list margin
+                    const float4 hq = w.hi[q];
+                    const float dx = hq.x - hp.x, dy = hq.y - hp.y, dz = hq.z - hp.z;
+                    const float r2 = dx * dx + dy * dy + dz * dz;
+                    if (r2 < rd2) {
+                        if (nd < capd) Ld[list_off(nd)] = (int)q;
+                        ++nd;
+                    }
+                    if (r2 < rn2) {
+                        if (nc < capc) Lc[list_off(nc)] = (int)q;
+                        ++nc;
+                    }
+                }
+            }
+        }
+    w.cnt_disp[p] = min(nd, capd);
+    w.cnt_cn[p] = min(nc, capc);
+    if (nd > capd || nc > capc) atomicOr(w.status, ST_LIST_CAP);
+    // per-structure maxima (one atomic per group of lanes in the same structure)
+    const unsigned mask = __activemask();
+    const unsigned grp = __match_any_sync(mask, s);
+    const int md = __reduce_max_sync(grp, nd), mc = __reduce_max_sync(grp, nc);
+    if ((threadIdx.x & 31) == __ffs(grp) - 1) {
+        atomicMax(&w.maxcnt[2 * s], md);
+        atomicMax(&w.maxcnt[2 * s + 1], mc);
+    }
+}
+
+inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+cudaError_t scan(const int* cnt, int* start, int* bsum, int64_t n, cudaStream_t st) {
+    const int nb = (int)nblk(n, kScanBlock);
+    k_scan_blocks<<<nb, kScanBlock, 0, st>>>(cnt, start, bsum, n);
+    k_scan_sums<<<1, kScanBlock, 0, st>>>(bsum, nb, start, n);
+    k_scan_add<<<nb, kScanBlock, 0, st>>>(start, bsum, n);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+// The cell-list build: binning, images, sort, fill, lists.  The caller has
+// zeroed cnt_real, cnt_ghost, ghost_count and maxcnt on the same stream.
+// bsum must hold nblk(ncells, 1024) ints; rk_tab holds k2*Rcov per type (bohr).
+cudaError_t launch_build_impl(const Work& w, const double* pos, const int32_t* types, const double* rk_tab,
+                              int* bsum, cudaStream_t st) {
+    if (w.Nr == 0) return cudaGetLastError();
+    const int TB = 256;
+    k_bin<<<nblk(w.Nr, TB), TB, 0, st>>>(w, pos, types);
+    cudaError_t e = scan(w.cnt_real, w.start_real, bsum, w.ncells, st);
+    if (e != cudaSuccess) return e;
+    e = scan(w.cnt_ghost, w.start_ghost, bsum, w.ncells, st);
+    if (e != cudaSuccess) return e;
+    k_scatter_real<<<nblk(w.Nr, TB), TB, 0, st>>>(w);
+    if (w.ghost_cap > 0) k_scatter_ghost<<<nblk(w.ghost_cap, TB), TB, 0, st>>>(w);
+    k_sort_cells<<<nblk(w.ncells, TB), TB, 0, st>>>(w);
+    k_fill_real<<<nblk(w.Nr, TB), TB, 0, st>>>(w, types, rk_tab);
+    if (w.ghost_cap > 0) k_fill_ghost<<<nblk(w.ghost_cap, TB), TB, 0, st>>>(w, types, rk_tab);
+    k_build_lists<<<nblk(w.Nr, 128), 128, 0, st>>>(w);
+    return cudaGetLastError();
+}
+
+int64_t scan_scratch_ints(int64_t ncells) { return nblk(ncells, kScanBlock) + 1; }
+
+}  // namespace d3gb

@@ -1,0 +1,187 @@
+// d3gb_internal.cuh -- shared device-side types of the D3(BJ) library.
+//
+// Data layout in device memory (one "plan" per batch geometry):
+//   real atoms   sorted by (structure, cell); structure s owns sorted slots
+//                [atom_base_s, atom_base_s + natoms_s), the same range it has
+//                in the caller's input order.
+//   image atoms  ("ghosts") periodic images of real atoms that fall inside the
+//                list radius of the cell; stored after the real atoms, sorted
+//                by cell.  Atom index q < Nr is real, q >= Nr is an image.
+//   per atom q   pos64[q] = (x, y, z, k2*Rcov) in bohr, FP64
+//                hi[q], lo[q] = FP32 split of the position (x = hi + lo) with
+//                hi.w = type | (data source << 4) as int bits, lo.w = k2*Rcov
+//   lists        per structure, blocked: atoms in groups of 32 by local index
+//                l = p - atom_base_s; entry k of atom l is at
+//                list_base_s + (l / 32) * cap_s * 32 + (k / 8) * 256 + (l % 32) * 8 + k % 8,
+//                so each lane owns whole 32-byte sectors (8 entries) and a warp
+//                reads 4 entries per lane with one coalesced 16-byte load.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace d3gb {
+
+// 32-byte aligned quadruple of doubles (one memory sector per load).
+struct __align__(32) dbl4 {
+    double x, y, z, w;
+};
+__host__ __device__ inline dbl4 dbl4_make(double x, double y, double z, double w) { return dbl4{x, y, z, w}; }
+
+constexpr double kBohrA = 0.529177210903;       // A per bohr
+constexpr double kHartreeEV = 27.211386245988;  // eV per Hartree
+constexpr int kMaxTypes = 16;
+constexpr int kMaxRef = 7;
+constexpr int kChunk = 64;  // pairs summed in FP32 before an FP64 accumulate (mixed form)
+
+enum StatusBits : int {
+    ST_GHOST_CAP = 1,
+    ST_LIST_CAP = 2,
+    ST_NONFINITE = 4,
+    ST_TYPE = 8,
+};
+
+// Per-structure geometry, computed on the host from the cell and pbc.
+struct StructGeo {
+    double H[9];      // lattice rows, bohr
+    double Hinv[9];   // inverse: f = x * Hinv
+    double lo[3];     // fractional coordinate of the grid origin along each axis
+    double fscale[3]; // grid cells per unit of fractional coordinate
+    double ext_lo[3], ext_hi[3];  // fractional window of image atoms (periodic axes)
+    int ncell[3];
+    int win[3];       // window half-width (cells) covering the list radius
+    int img[3];       // image range, 0 along open axes
+    int pbc[3];
+    int64_t cell_base;
+    int64_t atom_base;
+    int32_t natoms;
+    int32_t cap_disp, cap_cn;
+    int32_t pad;
+    int64_t list_base_disp, list_base_cn;
+};
+
+// Pointers and sizes of one plan's workspace, passed by value to kernels.
+struct Work {
+    const StructGeo* geo;
+    const int64_t* offsets;  // [B+1]
+    int B;
+    int64_t Nr;              // real atoms
+    int64_t ncells;          // total cells
+    int ghost_cap;
+    int T, R, RP;            // types, references, padded references
+    // binning
+    int* cnt_real;           // [ncells + 1]
+    int* cnt_ghost;          // [ncells + 1]
+    int* start_real;         // [ncells + 1]
+    int* start_ghost;        // [ncells + 1]
+    int* cell_of;            // [Nr] input order
+    int* slot_of;            // [Nr]
+    double* xw;              // [Nr*3] wrapped positions, bohr, input order
+    int* ghost_src;          // [ghost_cap] input index of the source atom
+    int* ghost_shift;        // [ghost_cap] packed lattice translation
+    int* ghost_cell;         // [ghost_cap]
+    int* ghost_slot;         // [ghost_cap]
+    int* ghost_count;        // [1]
+    int* sorted_src;         // [Nr] sorted -> input index
+    int* gsorted;            // [ghost_cap] sorted image slot -> raw image record
+    // per atom, sorted
+    dbl4* pos64;          // [Nr + ghost_cap]
+    float4* hi;              // [Nr + ghost_cap]
+    float4* lo;              // [Nr + ghost_cap]
+    int* perm;               // [Nr] sorted -> input index
+    int* sid;                // [Nr] structure of sorted real atom
+    int* cell_sorted;        // [Nr] global cell id of sorted real atom
+    // neighbour lists
+    int* nbr_disp;
+    int* nbr_cn;
+    int* cnt_disp;           // [Nr]
+    int* cnt_cn;             // [Nr]
+    int* maxcnt;             // [2*B] max list length per structure (disp, cn)
+    float rl_disp2, rl_cn2;  // list radii squared, bohr^2
+    // passes
+    double* cn;              // [Nr]
+    void* W;                 // [Nr][RP] real
+    void* dW;                // [Nr][RP] real
+    void* v;                 // [Nr][T][RP] real: v_q^(t)_a = sum_b C6ref[t][tq][a][b] W_qb
+    void* dEdn;              // [Nr] real
+    void* Fd;                // [Nr][4] real (direct forces)
+    double* eat;             // [Nr] site energies, Ha
+    double* wv;              // [Nr][6] per-atom virial (xx yy zz xy xz yz), Ha
+    double* fin_part;        // [B][ceil(max_natoms / 4096)][7] chunk sums
+    int64_t max_natoms;
+    int* status;
+};
+
+// Per-handle constants of the pair arithmetic.
+struct Consts {
+    double rc_disp2, rc_cn2;   // bohr^2
+    double k1, k3;
+    double s6, s8, a1, a2;     // damping of Eq. 2 (a2 in bohr)
+    int T, R, RP;
+};
+
+// ---- blocked neighbour lists
+__host__ __device__ inline int64_t list_row(int64_t base, int64_t local, int cap) {
+    return base + (local >> 5) * (int64_t)cap * 32 + (local & 31) * 8;
+}
+__host__ __device__ inline int list_off(int k) { return (k >> 3) * 256 + (k & 7); }
+__host__ __device__ inline int round_cap(double c) {
+    int v = (int)c;
+    return (v + 7) & ~7;
+}
+__host__ __device__ inline int64_t list_size(int64_t natoms, int cap) { return ((natoms + 31) >> 5) * 32 * (int64_t)cap; }
+
+struct ListView {
+    const int* p;  // the atom's row (list_row)
+    // fn(q) for entries [k0, k1); k0 must be a multiple of 4
+    template <class Fn>
+    __device__ __forceinline__ void for_each(int k0, int k1, Fn&& fn) const {
+        for (int k = k0; k < k1; k += 4) {
+            const int4 q4 = __ldg(reinterpret_cast<const int4*>(p + list_off(k)));
+            fn(q4.x);
+            if (k + 1 < k1) fn(q4.y);
+            if (k + 2 < k1) fn(q4.z);
+            if (k + 3 < k1) fn(q4.w);
+        }
+    }
+};
+
+__host__ __device__ inline int pack_shift(int a, int b, int c) {
+    return (a + 128) | ((b + 128) << 8) | ((c + 128) << 16);
+}
+__host__ __device__ inline void unpack_shift(int s, int& a, int& b, int& c) {
+    a = (s & 255) - 128;
+    b = ((s >> 8) & 255) - 128;
+    c = ((s >> 16) & 255) - 128;
+}
+
+// Structure of input atom i (binary search over offsets).
+__device__ inline int struct_of(const int64_t* off, int B, int64_t i) {
+    int lo = 0, hi = B;  // off[lo] <= i < off[hi]
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (off[mid] <= i) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+}  // namespace d3gb
+
+// Launchers implemented in the build and pass translation units.
+namespace d3gb {
+cudaError_t launch_build(const Work& w, const double* pos, const int32_t* types, cudaStream_t st);
+// Device tables of one handle.
+struct Tabs {
+    const void* c6;        // [T][T][R][R] real (float or double by precision)
+    const void* pair;      // [T][T] real4: R^6, R^8, s6, s8 R0^2
+    const double* cnref;   // [T][R]
+    const int* nref;       // [T]
+    const float4* rcpair;  // [T][T] k2 (Rcov_i + Rcov_j) as hi, lo and its square as hi, lo (bohr)
+};
+
+// marks (optional): 6 events recorded before the CN pass and after the CN,
+// weight, dispersion, chain and finalize passes.
+cudaError_t launch_forward(const Work& w, const Consts& c, bool mixed, const Tabs& tabs, double* E, double* F,
+                           double* W, double* e_atom, double* cn_out, int B, cudaStream_t st, cudaEvent_t* marks);
+constexpr int kForwardLaunches = 6;  // kernels per forward pass (B > 0, N > 0)
+constexpr int kBuildLaunches = 12;   // kernels per neighbour build (N > 0, with images)
+}  // namespace d3gb

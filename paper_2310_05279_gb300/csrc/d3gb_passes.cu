@@ -1,0 +1,532 @@
+// d3gb_passes.cu -- per-step passes of the D3(BJ) pipeline (arXiv 2310.05279,
+// Sec. II A), evaluated with full per-atom neighbour lists: the thread of atom i
+// visits every ordered pair instance (i, j) and writes only atom i's results,
+// so no pass needs atomics and every sum has a fixed order.
+//
+//   k_cn       Eq. 4  n_i = sum_j 1/(1 + exp(-k1 (k2 (Rcov_i + Rcov_j)/r - 1)))
+//   k_weights  Eq. 3  per-atom normalised Gaussian weights W_ia, dW_ia/dn_i and
+//                     the projections v_i^(t)_a = sum_b C6ref[t][t_i][a][b] W_ib,
+//                     so that C6_ij = sum_a W_ia v_j^(t_i)_a
+//   k_disp     Eq. 2  site energy, direct forces, virial and
+//                     dE/dn_i = sum_j (dE/dC6_ij)(dC6_ij/dn_i)
+//   k_chain           forces and virial of the coordination-number dependence:
+//                     F_i += sum_j (dE/dn_i + dE/dn_j) f'(r_ij) r_ij/r
+//   k_fin_*           per-structure energy and virial (fixed-order sums)
+//
+// MIXED = true: pair arithmetic in FP32 on split (hi + lo) positions, partial
+// sums promoted to FP64 every kChunk pairs; cutoff tests that fall within the
+// FP32 error band of the cutoff are decided in FP64, so the set of pairs is
+// the FP64 one.  MIXED = false: FP64 throughout.
+#include "d3gb_internal.cuh"
+
+namespace d3gb {
+
+namespace {
+
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float ex2_approx(float x) {
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float rsqrt_approx(float x) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+// one Newton step on the hardware estimates
+__device__ __forceinline__ float rsqrt_nr(float x) {
+    float y = rsqrt_approx(x);
+    float h = 0.5f * x * y;
+    return y * fmaf(-h, y, 1.5f);
+}
+__device__ __forceinline__ float rcp_nr(float x) {
+    float y = rcp_approx(x);
+    float e = fmaf(-x, y, 1.0f);
+    return fmaf(y, e, y);
+}
+
+// s + err == a + b exactly (Knuth's TwoSum)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& err) {
+    s = a + b;
+    const float bb = s - a;
+    err = (a - (s - bb)) + (b - bb);
+}
+// running compensated sum (value hi + lo)
+__device__ __forceinline__ void acc_add(float& hi, float& lo, float x) {
+    float s, e;
+    two_sum(hi, x, s, e);
+    hi = s;
+    lo += e;
+}
+__device__ __forceinline__ void acc_add(double& hi, double&, double x) { hi += x; }
+
+template <bool MIXED> struct Real;
+template <> struct Real<true> { using T = float; using T4 = float4; };
+template <> struct Real<false> { using T = double; using T4 = dbl4; };
+
+// Per-thread view of atom p's position and the distance to a neighbour q.
+template <bool MIXED> struct Site;
+
+template <> struct Site<true> {
+    float4 h, l;
+    const Work* w;
+    int64_t p;
+    __device__ Site(const Work& W, int64_t P) : w(&W), p(P) { h = W.hi[P]; l = W.lo[P]; }
+    __device__ int tsrc() const { return __float_as_int(h.w); }
+    __device__ float rk() const { return l.w; }
+    // distance vector to q; returns the neighbour's packed type/source and k2*Rcov
+    __device__ void dist(int q, float& dx, float& dy, float& dz, float& r2, int& tq, float& rkq) const {
+        const float4 hq = w->hi[q], lq = w->lo[q];
+        dx = (hq.x - h.x) + (lq.x - l.x);
+        dy = (hq.y - h.y) + (lq.y - l.y);
+        dz = (hq.z - h.z) + (lq.z - l.z);
+        r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        tq = __float_as_int(hq.w);
+        rkq = lq.w;
+    }
+    // exact pair vector as D + e (hi parts lie on a common grid, so hq - hp is exact)
+    __device__ void dist_exact(int q, float (&D)[3], float (&e)[3], int& tq) const {
+        const float4 hq = w->hi[q], lq = w->lo[q];
+        const float A[3] = {hq.x - h.x, hq.y - h.y, hq.z - h.z};
+        const float Bv[3] = {lq.x - l.x, lq.y - l.y, lq.z - l.z};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            D[k] = A[k] + Bv[k];
+            e[k] = Bv[k] - (D[k] - A[k]);  // |A| >= |B| unless A == 0: Fast2Sum is exact
+        }
+        tq = __float_as_int(hq.w);
+    }
+    // r^2 < rc2 as FP64 decides it: FP32 outside the error band, FP64 inside
+    __device__ bool inside(int q, float r2, float rc2f, double rc2d) const {
+        if (fabsf(r2 - rc2f) > 4e-6f * rc2f) return r2 < rc2f;
+        const dbl4 a = w->pos64[p], b = w->pos64[q];
+        const double ex = b.x - a.x, ey = b.y - a.y, ez = b.z - a.z;
+        return ex * ex + ey * ey + ez * ez < rc2d;
+    }
+};
+
+template <> struct Site<false> {
+    dbl4 x;
+    int ts;
+    const Work* w;
+    __device__ Site(const Work& W, int64_t P) : w(&W) { x = W.pos64[P]; ts = __float_as_int(W.hi[P].w); }
+    __device__ int tsrc() const { return ts; }
+    __device__ double rk() const { return x.w; }
+    __device__ void dist(int q, double& dx, double& dy, double& dz, double& r2, int& tq, double& rkq) const {
+        const dbl4 y = w->pos64[q];
+        dx = y.x - x.x;
+        dy = y.y - x.y;
+        dz = y.z - x.z;
+        r2 = dx * dx + dy * dy + dz * dz;
+        tq = __float_as_int(w->hi[q].w);
+        rkq = y.w;
+    }
+    __device__ bool inside(int, double r2, double rc2, double) const { return r2 < rc2; }
+};
+
+// Eq. 4 counting function f(r) and, optionally, df/dr; r from 1/r.
+__device__ __forceinline__ void cn_fun(float rinv, float rc_eff, float k1l2e, float k1, float& f, float* dfdr) {
+    // exp(-k1 (rc_eff/r - 1)) = 2^(k1 log2(e) (1 - rc_eff/r))
+    const float t = ex2_approx(k1l2e * fmaf(-rc_eff, rinv, 1.0f));
+    f = rcp_nr(1.0f + t);
+    if (dfdr) *dfdr = -k1 * rc_eff * rinv * rinv * t * f * f;
+}
+__device__ __forceinline__ void cn_fun(double rinv, double rc_eff, double, double k1, double& f, double* dfdr) {
+    const double t = exp(-k1 * (rc_eff * rinv - 1.0));
+    f = 1.0 / (1.0 + t);
+    if (dfdr) *dfdr = -k1 * rc_eff * rinv * rinv * t * f * f;
+}
+__device__ __forceinline__ float inv_sqrt(float x) { return rsqrt_nr(x); }
+__device__ __forceinline__ double inv_sqrt(double x) { return 1.0 / sqrt(x); }
+__device__ __forceinline__ float recip(float x) { return rcp_approx(x); }
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+
+template <int R, class T>
+__device__ __forceinline__ void load_vec(const T* __restrict__ p, T (&x)[R]) {
+#pragma unroll
+    for (int a = 0; a < R; ++a) x[a] = p[a];
+}
+template <int R>
+__device__ __forceinline__ void load_vec(const float* __restrict__ p, float (&x)[R]) {
+#pragma unroll
+    for (int a = 0; a < R; a += 4) {
+        const float4 t = __ldg(reinterpret_cast<const float4*>(p + a));
+        x[a] = t.x;
+        if (a + 1 < R) x[a + 1] = t.y;
+        if (a + 2 < R) x[a + 2] = t.z;
+        if (a + 3 < R) x[a + 3] = t.w;
+    }
+}
+
+
+// Mixed form: pair vector D (FP32), r^2 and the Eq. 4 exponent a = k1 (rc/r - 1)
+// with an error relative to a itself (see k_cn).  Returns false when the pair
+// is outside R_cn.
+__device__ __forceinline__ bool cn_pair_precise(const Site<true>& S, int q, const float4* rrow, float k1, float rc2,
+                                                double rc2d, float (&D)[3], float& r2, float& a, float& rch,
+                                                int& tq) {
+    float e[3];
+    S.dist_exact(q, D, e, tq);
+    float P[3], pl[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        P[k] = D[k] * D[k];
+        pl[k] = fmaf(D[k], D[k], -P[k]);
+    }
+    float S1, s1, Sh, s2;
+    two_sum(P[0], P[1], S1, s1);
+    two_sum(S1, P[2], Sh, s2);
+    const float Sl = (s1 + s2) + (pl[0] + pl[1] + pl[2]) + 2.0f * (D[0] * e[0] + D[1] * e[1] + D[2] * e[2]);
+    r2 = Sh + Sl;
+    if (!S.inside(q, r2, rc2, rc2d)) return false;
+    const float4 rc = rrow[tq & 15];  // rc_hi, rc_lo, rc^2 hi, rc^2 lo
+    const float u = (rc.z - Sh) + (rc.w - Sl);
+    const float r = r2 * rsqrt_nr(r2);
+    a = k1 * u * rcp_nr(r * ((rc.x + rc.y) + r));
+    rch = rc.x;
+    return true;
+}
+
+// ------------------------------------------------------------------ Eq. 4
+// The coordination numbers feed dC6/dn, which can be large, so the mixed form
+// keeps n_i accurate to a few 1e-8: the pair vector is exact (D + e), r^2 is
+// formed in double-single, the argument k1 (rc/r - 1) is evaluated as
+// k1 (rc^2 - r^2) / (r (rc + r)) so its error is relative to its own size,
+// and the sum over neighbours is compensated.
+template <bool MIXED>
+__global__ void __launch_bounds__(128) k_cn(Work w, Consts c, const float4* __restrict__ rcpair) {
+    using T = typename Real<MIXED>::T;
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= w.Nr) return;
+    const Site<MIXED> S(w, p);
+    const StructGeo& G = w.geo[w.sid[p]];
+    const ListView LV{w.nbr_cn + list_row(G.list_base_cn, p - G.atom_base, G.cap_cn)};
+    const int cnt = w.cnt_cn[p];
+    const T rc2 = (T)c.rc_cn2, k1 = (T)c.k1;
+    T nh = 0, nl = 0;
+    if constexpr (MIXED) {
+        const float4* rrow = rcpair + (S.tsrc() & 15) * c.T;
+        LV.for_each(0, cnt, [&](int q) {
+            float D[3], r2, a, rch;
+            int tq;
+            if (!cn_pair_precise(S, q, rrow, k1, rc2, c.rc_cn2, D, r2, a, rch, tq)) return;
+            acc_add(nh, nl, rcp_nr(1.0f + expf(-a)));
+        });
+        w.cn[p] = (double)nh + (double)nl;
+    } else {
+        const T rki = S.rk();
+        LV.for_each(0, cnt, [&](int q) {
+            T dx, dy, dz, r2, rkq;
+            int tq;
+            S.dist(q, dx, dy, dz, r2, tq, rkq);
+            if (!S.inside(q, r2, rc2, c.rc_cn2)) return;
+            T f;
+            cn_fun(inv_sqrt(r2), rki + rkq, (T)0, k1, f, (T*)nullptr);
+            nh += f;
+        });
+        w.cn[p] = (double)nh;
+    }
+}
+
+// ------------------------------------------------------------------ Eq. 3
+template <bool MIXED, int R>
+__global__ void __launch_bounds__(128) k_weights(Work w, Consts c, const double* __restrict__ cnref,
+                                                 const int* __restrict__ nref,
+                                                 const typename Real<MIXED>::T* __restrict__ c6) {
+    using T = typename Real<MIXED>::T;
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= w.Nr) return;
+    const int t = __float_as_int(w.hi[p].w) & 15;
+    const double n = w.cn[p];
+    const int nr = nref[t];
+    T z[R], L[R], ex[R];
+    T emax = -(T)1e30;
+#pragma unroll
+    for (int a = 0; a < R; ++a) {
+        z[a] = (T)(n - cnref[t * R + a]);
+        ex[a] = -(T)c.k3 * z[a] * z[a];
+        if (a < nr) emax = ex[a] > emax ? ex[a] : emax;
+    }
+    T sum = 0;
+#pragma unroll
+    for (int a = 0; a < R; ++a) {
+        L[a] = a < nr ? exp(ex[a] - emax) : (T)0;
+        sum += L[a];
+    }
+    const T inv = (T)1 / sum;
+    T gbar = 0;
+#pragma unroll
+    for (int a = 0; a < R; ++a) {
+        L[a] *= inv;
+        gbar += L[a] * (-2 * (T)c.k3 * z[a]);
+    }
+    T* Wp = (T*)w.W + p * c.RP;
+    T* dWp = (T*)w.dW + p * c.RP;
+#pragma unroll
+    for (int a = 0; a < R; ++a) {
+        Wp[a] = L[a];
+        dWp[a] = L[a] * (-2 * (T)c.k3 * z[a] - gbar);
+    }
+    for (int a = R; a < c.RP; ++a) Wp[a] = dWp[a] = 0;
+    T* vp = (T*)w.v + p * c.T * c.RP;
+    for (int u = 0; u < c.T; ++u) {
+        const T* cu = c6 + ((size_t)(u * c.T + t) * R) * R;  // C6ref[u][t][a][b]
+#pragma unroll
+        for (int a = 0; a < R; ++a) {
+            T s = 0;
+#pragma unroll
+            for (int b = 0; b < R; ++b) s += cu[a * R + b] * L[b];
+            vp[u * c.RP + a] = s;
+        }
+        for (int a = R; a < c.RP; ++a) vp[u * c.RP + a] = 0;
+    }
+}
+
+// ------------------------------------------------------------------ Eq. 2
+// pair table per (t_i, t_j): x = R^6, y = R^8, z = s6, w = s8 R0^2 (bohr, R = a1 R0 + a2)
+template <bool MIXED, int R>
+__global__ void __launch_bounds__(128) k_disp(Work w, Consts c, const typename Real<MIXED>::T4* __restrict__ pair_tab) {
+    using T = typename Real<MIXED>::T;
+    using T4 = typename Real<MIXED>::T4;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T4* tab = reinterpret_cast<T4*>(smem_raw);
+    for (int k = threadIdx.x; k < c.T * c.T; k += blockDim.x) tab[k] = pair_tab[k];
+    __syncthreads();
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= w.Nr) return;
+    const Site<MIXED> S(w, p);
+    const int ti = S.tsrc() & 15;
+    T Wi[R], dWi[R];
+    load_vec<R>((const T*)w.W + p * c.RP, Wi);
+    load_vec<R>((const T*)w.dW + p * c.RP, dWi);
+    const T4* row = tab + ti * c.T;
+    const T* vbase = (const T*)w.v + ti * c.RP;
+    const int vstride = c.T * c.RP;
+    const StructGeo& G = w.geo[w.sid[p]];
+    const ListView LV{w.nbr_disp + list_row(G.list_base_disp, p - G.atom_base, G.cap_disp)};
+    const int cnt = w.cnt_disp[p];
+    const T rc2 = (T)c.rc_disp2;
+    T fx = 0, fy = 0, fz = 0;
+    T dnh = 0, dnl = 0;  // dE/dn_i, compensated (it scales the chain-rule forces)
+    double E = 0, Sxx = 0, Syy = 0, Szz = 0, Sxy = 0, Sxz = 0, Syz = 0;
+    for (int k0 = 0; k0 < cnt; k0 += kChunk) {
+        const int k1e = min(cnt, k0 + kChunk);
+        T e = 0, sxx = 0, syy = 0, szz = 0, sxy = 0, sxz = 0, syz = 0;
+        LV.for_each(k0, k1e, [&](int q) {
+            T dx, dy, dz, r2, rkq;
+            int tsq;
+            S.dist(q, dx, dy, dz, r2, tsq, rkq);
+            if (!S.inside(q, r2, rc2, c.rc_disp2)) return;
+            const T4 tb = row[tsq & 15];
+            T vq[R];
+            load_vec<R>(vbase + (int64_t)(tsq >> 4) * vstride, vq);
+            T C6 = 0, dC6 = 0;
+#pragma unroll
+            for (int a = 0; a < R; ++a) {
+                C6 = fma(Wi[a], vq[a], C6);
+                dC6 = fma(dWi[a], vq[a], dC6);
+            }
+            const T r4 = r2 * r2, r6 = r4 * r2, r8 = r4 * r4;
+            const T d6 = r6 + tb.x, d8 = r8 + tb.y;
+            const T pinv = recip(d6 * d8);
+            const T i6 = d8 * pinv, i8 = d6 * pinv;
+            const T t6 = tb.z * i6, t8 = tb.w * i8;
+            const T g = t6 + t8;                     // -de/dC6
+            e = fma(-C6, g, e);
+            acc_add(dnh, dnl, -g * dC6);
+            // 2 de/d(r^2): F_i += (de/dr) d/r = fc d
+            const T fc = C6 * fma((T)6 * r4, t6 * i6, (T)8 * r6 * (t8 * i8));
+            const T tx = fc * dx, ty = fc * dy, tz = fc * dz;
+            fx += tx; fy += ty; fz += tz;
+            sxx = fma(tx, dx, sxx); syy = fma(ty, dy, syy); szz = fma(tz, dz, szz);
+            sxy = fma(tx, dy, sxy); sxz = fma(tx, dz, sxz); syz = fma(ty, dz, syz);
+        });
+        E += (double)e;
+        Sxx += (double)sxx; Syy += (double)syy; Szz += (double)szz;
+        Sxy += (double)sxy; Sxz += (double)sxz; Syz += (double)syz;
+    }
+    ((T*)w.dEdn)[p] = (T)((double)dnh + (double)dnl);
+    ((T4*)w.Fd)[p] = T4{fx, fy, fz, (T)0};
+    w.eat[p] = 0.5 * E;
+    double* wv = w.wv + 6 * p;
+    wv[0] = -0.5 * Sxx; wv[1] = -0.5 * Syy; wv[2] = -0.5 * Szz;
+    wv[3] = -0.5 * Sxy; wv[4] = -0.5 * Sxz; wv[5] = -0.5 * Syz;
+}
+
+// ------------------------------------------------------------------ CN chain rule
+template <bool MIXED>
+__global__ void __launch_bounds__(128) k_chain(Work w, Consts c, const float4* __restrict__ rcpair,
+                                              double* __restrict__ F, double* __restrict__ e_atom,
+                                              double* __restrict__ cn_out) {
+    using T = typename Real<MIXED>::T;
+    using T4 = typename Real<MIXED>::T4;
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= w.Nr) return;
+    const Site<MIXED> S(w, p);
+    const T* dEdn = (const T*)w.dEdn;
+    const T dni = dEdn[p];
+    const StructGeo& G = w.geo[w.sid[p]];
+    const ListView LV{w.nbr_cn + list_row(G.list_base_cn, p - G.atom_base, G.cap_cn)};
+    const int cnt = w.cnt_cn[p];
+    const T rc2 = (T)c.rc_cn2, k1 = (T)c.k1;
+    T fx = 0, fy = 0, fz = 0;
+    double Sxx = 0, Syy = 0, Szz = 0, Sxy = 0, Sxz = 0, Syz = 0;
+    for (int k0 = 0; k0 < cnt; k0 += kChunk) {
+        const int k1e = min(cnt, k0 + kChunk);
+        T sxx = 0, syy = 0, szz = 0, sxy = 0, sxz = 0, syz = 0;
+        LV.for_each(k0, k1e, [&](int q) {
+            T dx, dy, dz, coef;
+            if constexpr (MIXED) {
+                float D[3], r2, a, rch;
+                int tq;
+                if (!cn_pair_precise(S, q, rcpair + (S.tsrc() & 15) * c.T, k1, rc2, c.rc_cn2, D, r2, a, rch, tq))
+                    return;
+                const float t = expf(-a);
+                const float f = rcp_nr(1.0f + t);
+                const float rinv = rsqrt_nr(r2);
+                const float dfdr = -k1 * rch * rinv * rinv * t * f * f;
+                coef = (dni + dEdn[tq >> 4]) * dfdr * rinv;
+                dx = D[0]; dy = D[1]; dz = D[2];
+            } else {
+                T r2, rkq;
+                int tsq;
+                S.dist(q, dx, dy, dz, r2, tsq, rkq);
+                if (!S.inside(q, r2, rc2, c.rc_cn2)) return;
+                const T rinv = inv_sqrt(r2);
+                T f, dfdr;
+                cn_fun(rinv, S.rk() + rkq, (T)0, k1, f, &dfdr);
+                coef = (dni + dEdn[tsq >> 4]) * dfdr * rinv;
+            }
+            const T tx = coef * dx, ty = coef * dy, tz = coef * dz;
+            fx += tx; fy += ty; fz += tz;
+            sxx = fma(tx, dx, sxx); syy = fma(ty, dy, syy); szz = fma(tz, dz, szz);
+            sxy = fma(tx, dy, sxy); sxz = fma(tx, dz, sxz); syz = fma(ty, dz, syz);
+        });
+        Sxx += (double)sxx; Syy += (double)syy; Szz += (double)szz;
+        Sxy += (double)sxy; Sxz += (double)sxz; Syz += (double)syz;
+    }
+    const T4 fd = ((const T4*)w.Fd)[p];
+    const double u = kHartreeEV / kBohrA;
+    const int i = w.perm[p];
+    F[3 * (int64_t)i + 0] = ((double)fd.x + (double)fx) * u;
+    F[3 * (int64_t)i + 1] = ((double)fd.y + (double)fy) * u;
+    F[3 * (int64_t)i + 2] = ((double)fd.z + (double)fz) * u;
+    double* wv = w.wv + 6 * p;
+    wv[0] -= 0.5 * Sxx; wv[1] -= 0.5 * Syy; wv[2] -= 0.5 * Szz;
+    wv[3] -= 0.5 * Sxy; wv[4] -= 0.5 * Sxz; wv[5] -= 0.5 * Syz;
+    if (e_atom) e_atom[i] = w.eat[p] * kHartreeEV;
+    if (cn_out) cn_out[i] = w.cn[p];
+}
+
+// ------------------------------------------------------------------ per-structure sums
+// Two fixed-order levels: block (s, c) sums atoms [c*kFinChunk, (c+1)*kFinChunk)
+// of structure s into part[s][c][7]; one block per structure then adds its
+// chunks in order.  Deterministic for any batch shape.
+constexpr int kFinChunk = 4096;
+
+__global__ void __launch_bounds__(256) k_fin_chunks(Work w, double* __restrict__ part, int nchunk) {
+    const int s = blockIdx.x, ch = blockIdx.y;
+    const StructGeo& G = w.geo[s];
+    const int64_t k0 = (int64_t)ch * kFinChunk, k1 = k0 + kFinChunk < (int64_t)G.natoms ? k0 + kFinChunk : (int64_t)G.natoms;
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+        const int64_t p = G.atom_base + k;
+        acc[0] += w.eat[p];
+#pragma unroll
+        for (int m = 0; m < 6; ++m) acc[1 + m] += w.wv[6 * p + m];
+    }
+    __shared__ double red[7][256];
+#pragma unroll
+    for (int m = 0; m < 7; ++m) red[m][threadIdx.x] = acc[m];
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o)
+#pragma unroll
+            for (int m = 0; m < 7; ++m) red[m][threadIdx.x] += red[m][threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x < 7) part[((int64_t)s * nchunk + ch) * 7 + threadIdx.x] = red[threadIdx.x][0];
+}
+
+__global__ void k_fin_struct(Work w, const double* __restrict__ part, int nchunk, double* __restrict__ E,
+                             double* __restrict__ Wout) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= w.B) return;
+    const int nc = (w.geo[s].natoms + kFinChunk - 1) / kFinChunk;
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int ch = 0; ch < nc; ++ch)
+#pragma unroll
+        for (int m = 0; m < 7; ++m) acc[m] += part[((int64_t)s * nchunk + ch) * 7 + m];
+    const double h = kHartreeEV;
+    E[s] = acc[0] * h;
+    double* Ws = Wout + 9 * (int64_t)s;
+    Ws[0] = acc[1] * h; Ws[4] = acc[2] * h; Ws[8] = acc[3] * h;
+    Ws[1] = Ws[3] = acc[4] * h;
+    Ws[2] = Ws[6] = acc[5] * h;
+    Ws[5] = Ws[7] = acc[6] * h;
+}
+
+inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+template <bool MIXED, int R>
+cudaError_t forward_impl(const Work& w, const Consts& c, const Tabs& tb, double* E, double* F, double* W,
+                         double* e_atom, double* cn_out, int B, cudaStream_t st, cudaEvent_t* marks) {
+    using T = typename Real<MIXED>::T;
+    using T4 = typename Real<MIXED>::T4;
+    const int TB = 128;
+    auto mark = [&](int k) {
+        if (marks) cudaEventRecord(marks[k], st);
+    };
+    mark(0);
+    if (w.Nr > 0) k_cn<MIXED><<<nblk(w.Nr, TB), TB, 0, st>>>(w, c, tb.rcpair);
+    mark(1);
+    if (w.Nr > 0) k_weights<MIXED, R><<<nblk(w.Nr, TB), TB, 0, st>>>(w, c, tb.cnref, tb.nref, (const T*)tb.c6);
+    mark(2);
+    if (w.Nr > 0) k_disp<MIXED, R><<<nblk(w.Nr, TB), TB, c.T * c.T * sizeof(T4), st>>>(w, c, (const T4*)tb.pair);
+    mark(3);
+    if (w.Nr > 0) k_chain<MIXED><<<nblk(w.Nr, TB), TB, 0, st>>>(w, c, tb.rcpair, F, e_atom, cn_out);
+    mark(4);
+    if (B > 0) {
+        const int nchunk = (int)((w.max_natoms + kFinChunk - 1) / kFinChunk);
+        if (nchunk > 0) k_fin_chunks<<<dim3(B, nchunk), 256, 0, st>>>(w, w.fin_part, nchunk);
+        k_fin_struct<<<nblk(B, 128), 128, 0, st>>>(w, w.fin_part, nchunk > 0 ? nchunk : 1, E, W);
+    }
+    mark(5);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_forward(const Work& w, const Consts& c, bool mixed, const Tabs& tabs, double* E, double* F,
+                           double* W, double* e_atom, double* cn_out, int B, cudaStream_t st, cudaEvent_t* marks) {
+#define D3_FWD(M, RR) return forward_impl<M, RR>(w, c, tabs, E, F, W, e_atom, cn_out, B, st, marks)
+    if (mixed) {
+        switch (c.R) {
+            case 1: D3_FWD(true, 1);
+            case 2: D3_FWD(true, 2);
+            case 3: D3_FWD(true, 3);
+            case 4: D3_FWD(true, 4);
+            case 5: D3_FWD(true, 5);
+            case 6: D3_FWD(true, 6);
+            default: D3_FWD(true, 7);
+        }
+    } else {
+        switch (c.R) {
+            case 1: D3_FWD(false, 1);
+            case 2: D3_FWD(false, 2);
+            case 3: D3_FWD(false, 3);
+            case 4: D3_FWD(false, 4);
+            case 5: D3_FWD(false, 5);
+            case 6: D3_FWD(false, 6);
+            default: D3_FWD(false, 7);
+        }
+    }
+#undef D3_FWD
+}
+
+}  // namespace d3gb

@@ -12,6 +12,8 @@ import pytest
 
 from paper_2310_05279_gb300 import workloads as wl
 
+from ._helpers import cluster_around
+
 PRM = dict(wl.PBE_BJ)
 
 
@@ -159,27 +161,6 @@ def test_site_energies_sum(oracle_mod):
     r = oracle_mod.compute(pos, types, cell, [1, 1, 1], tabs, PRM)
     assert abs(r["e_atom"].sum() - r["E"]) <= 1e-13 * abs(r["E"])
     assert np.all(r["e_atom"] < 0)
-
-
-def cluster_around(pos, types, cell, i, radius):
-    """All images of all atoms within `radius` of atom i, centre atom first."""
-    inv = np.linalg.inv(cell)
-    widths = abs(np.linalg.det(cell)) / np.linalg.norm(np.cross(cell[[1, 2, 0]], cell[[2, 0, 1]]), axis=1)
-    m = np.ceil(radius / widths).astype(int) + 1
-    d0 = pos - pos[i]
-    d0 -= np.floor(d0 @ inv + 0.5) @ cell
-    out_p, out_t = [np.zeros(3)], [types[i]]
-    for n0 in range(-m[0], m[0] + 1):
-        for n1 in range(-m[1], m[1] + 1):
-            for n2 in range(-m[2], m[2] + 1):
-                d = d0 + np.array([n0, n1, n2]) @ cell
-                r = np.linalg.norm(d, axis=1)
-                sel = r < radius
-                if n0 == 0 and n1 == 0 and n2 == 0:
-                    sel[i] = False
-                out_p.append(d[sel])
-                out_t.append(types[sel])
-    return np.vstack([np.atleast_2d(x) for x in out_p]), np.concatenate([np.atleast_1d(t) for t in out_t])
 
 
 def test_locality_of_forces(oracle_mod):

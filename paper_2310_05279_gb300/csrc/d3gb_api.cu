@@ -293,6 +293,7 @@ d3_status plan_alloc(d3_handle* h, Plan& P) {
     A(w.ghost_shift, int, Ng);
     A(w.ghost_cell, int, Ng);
     A(w.ghost_slot, int, Ng);
+    A(w.ghost_sid, int, Ng);
     A(w.ghost_count, int, 1);
     A(w.sorted_src, int, Nr);
     A(w.gsorted, int, Ng);

@@ -42,60 +42,106 @@ __device__ inline int warp_aggregated_inc(int* ctr) {
     return base + rank;
 }
 
-__global__ void k_bin(Work w, const double* __restrict__ pos, const int32_t* __restrict__ types) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= w.Nr) return;
-    const int s = struct_of(w.offsets, w.B, i);
-    const StructGeo& G = w.geo[s];
-    double xb[3];
-    bool fin = true;
+// Wrap, bin, and emit image atoms.  Image slots are reserved once per block:
+// each thread counts its kept images, the block scans the counts in shared
+// memory and one thread reserves the block's range with a single atomic.
+__global__ void __launch_bounds__(256) k_bin(Work w, const double* __restrict__ pos, const int32_t* __restrict__ types) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = i < w.Nr;
+    int s = 0;
+    double f[3] = {0, 0, 0};
+    if (live) {
+        s = struct_of(w.offsets, w.B, i);
+        const StructGeo& G = w.geo[s];
+        double xb[3];
+        bool fin = true;
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        xb[a] = pos[3 * i + a] * (1.0 / kBohrA);
-        fin = fin && isfinite(xb[a]);
-    }
-    if (!fin) {
-        atomicOr(w.status, ST_NONFINITE);
-        xb[0] = xb[1] = xb[2] = 0.0;
-    }
-    const int t = types[i];
-    if (t < 0 || t >= w.T) atomicOr(w.status, ST_TYPE);
-    double f[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        f[k] = xb[0] * G.Hinv[k] + xb[1] * G.Hinv[3 + k] + xb[2] * G.Hinv[6 + k];
-        if (G.pbc[k]) {
-            f[k] -= floor(f[k]);
-            if (f[k] >= 1.0) f[k] -= 1.0;
+        for (int a = 0; a < 3; ++a) {
+            xb[a] = pos[3 * i + a] * (1.0 / kBohrA);
+            fin = fin && isfinite(xb[a]);
         }
-    }
+        if (!fin) {
+            atomicOr(w.status, ST_NONFINITE);
+            xb[0] = xb[1] = xb[2] = 0.0;
+        }
+        const int t = types[i];
+        if (t < 0 || t >= w.T) atomicOr(w.status, ST_TYPE);
 #pragma unroll
-    for (int a = 0; a < 3; ++a) w.xw[3 * i + a] = f[0] * G.H[a] + f[1] * G.H[3 + a] + f[2] * G.H[6 + a];
-    const int cid = cell_id(G, f);
-    w.cell_of[i] = cid;
-    w.slot_of[i] = atomicAdd(&w.cnt_real[cid], 1);
-
-    // periodic images that land inside the margin of the grid
+        for (int k = 0; k < 3; ++k) {
+            f[k] = xb[0] * G.Hinv[k] + xb[1] * G.Hinv[3 + k] + xb[2] * G.Hinv[6 + k];
+            if (G.pbc[k]) {
+                f[k] -= floor(f[k]);
+                if (f[k] >= 1.0) f[k] -= 1.0;
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) w.xw[3 * i + a] = f[0] * G.H[a] + f[1] * G.H[3 + a] + f[2] * G.H[6 + a];
+        const int cid = cell_id(G, f);
+        w.cell_of[i] = cid;
+        w.slot_of[i] = atomicAdd(&w.cnt_real[cid], 1);
+    }
+    const StructGeo& G = w.geo[s];
+    auto kept = [&](int n0, int n1, int n2, double g[3]) {
+        g[0] = f[0] + n0;
+        g[1] = f[1] + n1;
+        g[2] = f[2] + n2;
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            if (G.img[k] > 0 && (g[k] < G.ext_lo[k] || g[k] >= G.ext_hi[k])) return false;
+        return true;
+    };
+    // pass 1: count
+    int mine = 0;
+    if (live)
+        for (int n0 = -G.img[0]; n0 <= G.img[0]; ++n0)
+            for (int n1 = -G.img[1]; n1 <= G.img[1]; ++n1)
+                for (int n2 = -G.img[2]; n2 <= G.img[2]; ++n2) {
+                    if (n0 == 0 && n1 == 0 && n2 == 0) continue;
+                    double g[3];
+                    if (kept(n0, n1, n2, g)) ++mine;
+                }
+    // block scan of the counts
+    __shared__ int wsum[8];
+    __shared__ int base;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int x = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[wid] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+            const int v = wsum[k];
+            wsum[k] = acc;
+            acc += v;
+        }
+        base = acc > 0 ? atomicAdd(w.ghost_count, acc) : 0;
+    }
+    __syncthreads();
+    if (!live || mine == 0) return;
+    int slot = base + wsum[wid] + x - mine;
+    // pass 2: write
     for (int n0 = -G.img[0]; n0 <= G.img[0]; ++n0)
         for (int n1 = -G.img[1]; n1 <= G.img[1]; ++n1)
             for (int n2 = -G.img[2]; n2 <= G.img[2]; ++n2) {
                 if (n0 == 0 && n1 == 0 && n2 == 0) continue;
-                const double g[3] = {f[0] + n0, f[1] + n1, f[2] + n2};
-                bool keep = true;
-#pragma unroll
-                for (int k = 0; k < 3; ++k)
-                    if (G.img[k] > 0 && (g[k] < G.ext_lo[k] || g[k] >= G.ext_hi[k])) keep = false;
-                if (!keep) continue;
-                const int slot = warp_aggregated_inc(w.ghost_count);
+                double g[3];
+                if (!kept(n0, n1, n2, g)) continue;
                 if (slot >= w.ghost_cap) {
                     atomicOr(w.status, ST_GHOST_CAP);
-                    continue;
+                    return;
                 }
                 const int gc = cell_id(G, g);
                 w.ghost_src[slot] = (int)i;
                 w.ghost_shift[slot] = pack_shift(n0, n1, n2);
                 w.ghost_cell[slot] = gc;
                 w.ghost_slot[slot] = atomicAdd(&w.cnt_ghost[gc], 1);
+                w.ghost_sid[slot] = s;
+                ++slot;
             }
 }
 
@@ -246,7 +292,7 @@ __global__ void k_fill_ghost(Work w, const int32_t* __restrict__ types, const do
     const int i = w.ghost_src[g];
     int n0, n1, n2;
     unpack_shift(w.ghost_shift[g], n0, n1, n2);
-    const StructGeo& G = w.geo[struct_of(w.offsets, w.B, i)];
+    const StructGeo& G = w.geo[w.ghost_sid[g]];
     int t = types[i];
     if (t < 0 || t >= w.T) t = 0;
     double x[3];
@@ -277,29 +323,39 @@ __global__ void k_build_lists(Work w) {
     const int z0 = max(0, c2 - G.win[2]), z1 = min(G.ncell[2] - 1, c2 + G.win[2]);
     const int y0 = max(0, c1 - G.win[1]), y1 = min(G.ncell[1] - 1, c1 + G.win[1]);
     const int x0 = max(0, c0 - G.win[0]), x1 = min(G.ncell[0] - 1, c0 + G.win[0]);
+    auto test = [&](int64_t q, float4 hq) {
+        // grid-aligned hi parts: error <= sqrt(3) 2^-10 bohr, covered by the list margin
+        const float dx = hq.x - hp.x, dy = hq.y - hp.y, dz = hq.z - hp.z;
+        const float r2 = dx * dx + dy * dy + dz * dz;
+        if (q == p) return;
+        if (r2 < rd2) {
+            if (nd < capd) Ld[list_off(nd)] = (int)q;
+            ++nd;
+        }
+        if (r2 < rn2) {
+            if (nc < capc) Lc[list_off(nc)] = (int)q;
+            ++nc;
+        }
+    };
+    const float4* __restrict__ H = w.hi;
     for (int z = z0; z <= z1; ++z)
         for (int y = y0; y <= y1; ++y) {
             const int64_t row = G.cell_base + ((int64_t)z * G.ncell[1] + y) * G.ncell[0];
+            const int rb = __ldg(&w.start_real[row + x0]), re = __ldg(&w.start_real[row + x1 + 1]);
+            const int gb = __ldg(&w.start_ghost[row + x0]), ge = __ldg(&w.start_ghost[row + x1 + 1]);
             for (int pass = 0; pass < 2; ++pass) {
-                const int* st = pass == 0 ? w.start_real : w.start_ghost;
                 const int64_t off = pass == 0 ? 0 : w.Nr;
-                const int b = st[row + x0], e = st[row + x1 + 1];
-                for (int u = b; u < e; ++u) {
-                    const int64_t q = off + u;
-                    if (q == p) continue;
-                    // grid-aligned hi parts: error <= sqrt(3) 2^-10 bohr, covered by the list margin
-                    const float4 hq = w.hi[q];
-                    const float dx = hq.x - hp.x, dy = hq.y - hp.y, dz = hq.z - hp.z;
-                    const float r2 = dx * dx + dy * dy + dz * dz;
-                    if (r2 < rd2) {
-                        if (nd < capd) Ld[list_off(nd)] = (int)q;
-                        ++nd;
-                    }
-                    if (r2 < rn2) {
-                        if (nc < capc) Lc[list_off(nc)] = (int)q;
-                        ++nc;
-                    }
+                const int b = pass == 0 ? rb : gb, e = pass == 0 ? re : ge;
+                int u = b;
+                for (; u + 4 <= e; u += 4) {
+                    const float4 h0 = __ldg(&H[off + u]), h1 = __ldg(&H[off + u + 1]);
+                    const float4 h2 = __ldg(&H[off + u + 2]), h3 = __ldg(&H[off + u + 3]);
+                    test(off + u, h0);
+                    test(off + u + 1, h1);
+                    test(off + u + 2, h2);
+                    test(off + u + 3, h3);
                 }
+                for (; u < e; ++u) test(off + u, __ldg(&H[off + u]));
             }
         }
     w.cnt_disp[p] = min(nd, capd);

@@ -80,6 +80,7 @@ struct Work {
     int* ghost_shift;        // [ghost_cap] packed lattice translation
     int* ghost_cell;         // [ghost_cap]
     int* ghost_slot;         // [ghost_cap]
+    int* ghost_sid;          // [ghost_cap] structure of the image
     int* ghost_count;        // [1]
     int* sorted_src;         // [Nr] sorted -> input index
     int* gsorted;            // [ghost_cap] sorted image slot -> raw image record

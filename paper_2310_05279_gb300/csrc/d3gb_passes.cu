@@ -165,11 +165,14 @@ __device__ __forceinline__ void load_vec(const float* __restrict__ p, float (&x)
 
 
 // Mixed form: pair vector D (FP32), r^2 and the Eq. 4 exponent a = k1 (rc/r - 1)
-// with an error relative to a itself (see k_cn).  Returns false when the pair
-// is outside R_cn.
+// as a double-single pair (ah + al) from the exact pair vector D + e:
+//   r^2 = Sh + Sl (TwoProd/TwoSum), u = rc^2 - r^2, r = sqrt(r^2) with its
+//   correction term, den = r^2 + r rc, a = k1 u / den with one residual step.
+// Its error is a few units of 2^-48 relative, so exp(-a) is as accurate as
+// expf itself.  Returns false when the pair is outside R_cn.
 __device__ __forceinline__ bool cn_pair_precise(const Site<true>& S, int q, const float4* rrow, float k1, float rc2,
-                                                double rc2d, float (&D)[3], float& r2, float& a, float& rch,
-                                                int& tq) {
+                                                double rc2d, float (&D)[3], float& r2, float& ah, float& al,
+                                                float& rch, int& tq) {
     float e[3];
     S.dist_exact(q, D, e, tq);
     float P[3], pl[3];
@@ -181,13 +184,25 @@ __device__ __forceinline__ bool cn_pair_precise(const Site<true>& S, int q, cons
     float S1, s1, Sh, s2;
     two_sum(P[0], P[1], S1, s1);
     two_sum(S1, P[2], Sh, s2);
-    const float Sl = (s1 + s2) + (pl[0] + pl[1] + pl[2]) + 2.0f * (D[0] * e[0] + D[1] * e[1] + D[2] * e[2]);
-    r2 = Sh + Sl;
+    float Sl = (s1 + s2) + (pl[0] + pl[1] + pl[2]) + 2.0f * (D[0] * e[0] + D[1] * e[1] + D[2] * e[2]);
+    two_sum(Sh, Sl, Sh, Sl);  // normalise
+    r2 = Sh;
     if (!S.inside(q, r2, rc2, rc2d)) return false;
-    const float4 rc = rrow[tq & 15];  // rc_hi, rc_lo, rc^2 hi, rc^2 lo
-    const float u = (rc.z - Sh) + (rc.w - Sl);
-    const float r = r2 * rsqrt_nr(r2);
-    a = k1 * u * rcp_nr(r * ((rc.x + rc.y) + r));
+    const float4 rc = rrow[tq & 15];  // rc hi, rc lo, rc^2 hi, rc^2 lo
+    float uh, ue;
+    two_sum(rc.z, -Sh, uh, ue);
+    const float ul = ue + (rc.w - Sl);
+    const float rh = Sh * rsqrt_nr(Sh);
+    const float rl = (fmaf(-rh, rh, Sh) + Sl) * (0.5f / rh);
+    const float ph = rh * rc.x, pe = fmaf(rh, rc.x, -ph);
+    float dh, de;
+    two_sum(Sh, ph, dh, de);
+    const float dl = de + Sl + pe + rh * rc.y + rl * rc.x;
+    const float idh = rcp_nr(dh);
+    const float qh = uh * idh;
+    const float ql = (fmaf(-qh, dh, uh) + ul - qh * dl) * idh;
+    ah = k1 * qh;
+    al = k1 * ql;
     rch = rc.x;
     return true;
 }
@@ -211,13 +226,21 @@ __global__ void __launch_bounds__(128) k_cn(Work w, Consts c, const float4* __re
     T nh = 0, nl = 0;
     if constexpr (MIXED) {
         const float4* rrow = rcpair + (S.tsrc() & 15) * c.T;
+        int nint = 0;  // terms with f > 1/2 are summed as 1 - t/(1 + t): exact integer part plus a small complement
         LV.for_each(0, cnt, [&](int q) {
-            float D[3], r2, a, rch;
+            float D[3], r2, ah, al, rch;
             int tq;
-            if (!cn_pair_precise(S, q, rrow, k1, rc2, c.rc_cn2, D, r2, a, rch, tq)) return;
-            acc_add(nh, nl, rcp_nr(1.0f + expf(-a)));
+            if (!cn_pair_precise(S, q, rrow, k1, rc2, c.rc_cn2, D, r2, ah, al, rch, tq)) return;
+            const float t = expf(-ah) * (1.0f - al);
+            const float f = rcp_nr(1.0f + t);
+            if (t < 1.0f) {
+                ++nint;
+                acc_add(nh, nl, -(t * f));
+            } else {
+                acc_add(nh, nl, f);
+            }
         });
-        w.cn[p] = (double)nh + (double)nl;
+        w.cn[p] = (double)nint + (double)nh + (double)nl;
     } else {
         const T rki = S.rk();
         LV.for_each(0, cnt, [&](int q) {
@@ -234,6 +257,10 @@ __global__ void __launch_bounds__(128) k_cn(Work w, Consts c, const float4* __re
 }
 
 // ------------------------------------------------------------------ Eq. 3
+// Per atom: the exponents -k3 (n - nref_a)^2 minus their maximum are formed in
+// FP64 (their absolute error sets the relative error of the weights), and
+// exp(y) is taken as exp(y_hi) (1 + y_lo).  dW_a/dn is written as
+// -2 k3 W_a sum_b W_b (nref_b - nref_a), which has no cancellation against n.
 template <bool MIXED, int R>
 __global__ void __launch_bounds__(128) k_weights(Work w, Consts c, const double* __restrict__ cnref,
                                                  const int* __restrict__ nref,
@@ -244,33 +271,43 @@ __global__ void __launch_bounds__(128) k_weights(Work w, Consts c, const double*
     const int t = __float_as_int(w.hi[p].w) & 15;
     const double n = w.cn[p];
     const int nr = nref[t];
-    T z[R], L[R], ex[R];
-    T emax = -(T)1e30;
+    double x[R];
+    double xmax = -1e300;
 #pragma unroll
     for (int a = 0; a < R; ++a) {
-        z[a] = (T)(n - cnref[t * R + a]);
-        ex[a] = -(T)c.k3 * z[a] * z[a];
-        if (a < nr) emax = ex[a] > emax ? ex[a] : emax;
+        const double z = n - cnref[t * R + a];
+        x[a] = -c.k3 * z * z;
+        if (a < nr && x[a] > xmax) xmax = x[a];
     }
+    T L[R];
     T sum = 0;
 #pragma unroll
     for (int a = 0; a < R; ++a) {
-        L[a] = a < nr ? exp(ex[a] - emax) : (T)0;
+        if (a < nr) {
+            const double y = x[a] - xmax;
+            if constexpr (MIXED) {
+                const float yh = (float)y, yl = (float)(y - (double)yh);
+                L[a] = expf(yh) * (1.0f + yl);
+            } else {
+                L[a] = exp(y);
+            }
+        } else {
+            L[a] = 0;
+        }
         sum += L[a];
     }
     const T inv = (T)1 / sum;
-    T gbar = 0;
 #pragma unroll
-    for (int a = 0; a < R; ++a) {
-        L[a] *= inv;
-        gbar += L[a] * (-2 * (T)c.k3 * z[a]);
-    }
+    for (int a = 0; a < R; ++a) L[a] *= inv;
     T* Wp = (T*)w.W + p * c.RP;
     T* dWp = (T*)w.dW + p * c.RP;
 #pragma unroll
     for (int a = 0; a < R; ++a) {
+        T s = 0;
+#pragma unroll
+        for (int b = 0; b < R; ++b) s += L[b] * (T)(cnref[t * R + b] - cnref[t * R + a]);
         Wp[a] = L[a];
-        dWp[a] = L[a] * (-2 * (T)c.k3 * z[a] - gbar);
+        dWp[a] = -2 * (T)c.k3 * L[a] * s;
     }
     for (int a = R; a < c.RP; ++a) Wp[a] = dWp[a] = 0;
     T* vp = (T*)w.v + p * c.T * c.RP;
@@ -382,11 +419,11 @@ __global__ void __launch_bounds__(128) k_chain(Work w, Consts c, const float4* _
         LV.for_each(k0, k1e, [&](int q) {
             T dx, dy, dz, coef;
             if constexpr (MIXED) {
-                float D[3], r2, a, rch;
+                float D[3], r2, ah, al, rch;
                 int tq;
-                if (!cn_pair_precise(S, q, rcpair + (S.tsrc() & 15) * c.T, k1, rc2, c.rc_cn2, D, r2, a, rch, tq))
+                if (!cn_pair_precise(S, q, rcpair + (S.tsrc() & 15) * c.T, k1, rc2, c.rc_cn2, D, r2, ah, al, rch, tq))
                     return;
-                const float t = expf(-a);
+                const float t = expf(-ah) * (1.0f - al);
                 const float f = rcp_nr(1.0f + t);
                 const float rinv = rsqrt_nr(r2);
                 const float dfdr = -k1 * rch * rinv * rinv * t * f * f;

@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -273,6 +274,12 @@ d3_status plan_alloc(d3_handle* h, Plan& P) {
     w.T = h->T;
     w.R = h->R;
     w.RP = h->RP;
+    {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        w.num_sms = sms > 0 ? sms : 1;
+    }
     const size_t rs = h->prm.precision == D3_MIXED ? sizeof(float) : sizeof(double);
     StructGeo* dgeo = nullptr;
     int64_t* doff = nullptr;
@@ -298,8 +305,9 @@ d3_status plan_alloc(d3_handle* h, Plan& P) {
     A(w.sorted_src, int, Nr);
     A(w.gsorted, int, Ng);
     A(w.pos64, dbl4, Nt);
-    A(w.hi, float4, Nt);
-    A(w.lo, float4, Nt);
+    A(w.rec, float4, 2 * Nt);
+    A(w.fw, double, 3 * Nr);
+    A(w.frange, int, 6 * (int64_t)B);
     A(w.perm, int, Nr);
     A(w.sid, int, Nr);
     A(w.cell_sorted, int, Nr);
@@ -308,6 +316,7 @@ d3_status plan_alloc(d3_handle* h, Plan& P) {
     A(w.cnt_disp, int, Nr);
     A(w.cnt_cn, int, Nr);
     A(w.maxcnt, int, 2 * B);
+    A(w.work_ctr, int, 1);
     A(w.cn, double, Nr);
     A(w.W, char, Nr * h->RP * rs);
     A(w.dW, char, Nr * h->RP * rs);
@@ -360,6 +369,10 @@ d3_status enqueue_build(d3_handle* h, Plan& P, const double* pos, const int32_t*
     if (e == cudaSuccess) e = cudaMemsetAsync(w.cnt_ghost, 0, sizeof(int) * (P.ncells + 1), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(w.ghost_count, 0, sizeof(int), st);
     if (e == cudaSuccess && P.B > 0) e = cudaMemsetAsync(w.maxcnt, 0, sizeof(int) * 2 * P.B, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(w.work_ctr, 0, sizeof(int), st);
+    // occupied-range minima start at a huge float, maxima at +0
+    if (e == cudaSuccess && P.B > 0) e = cudaMemsetAsync(w.frange, 0x7f, sizeof(int) * 3 * P.B, st);
+    if (e == cudaSuccess && P.B > 0) e = cudaMemsetAsync(w.frange + 3 * P.B, 0, sizeof(int) * 3 * P.B, st);
     if (e != cudaSuccess) return cuda_fail(h, e, "memset");
     e = launch_build_impl(w, pos, types, h->d_rk, P.bsum, st);
     if (e != cudaSuccess) return cuda_fail(h, e, "neighbour build launch");
@@ -511,7 +524,7 @@ d3_status d3_create(const d3_params* params, const d3_tables* tables, d3_handle*
     h->prm = p;
     h->T = T;
     h->R = R;
-    h->RP = (R + 3) / 4 * 4;
+    h->RP = R <= 4 ? 4 : 8;
     h->nref.assign(t.nref, t.nref + T);
     h->cnref.assign(t.cn_ref, t.cn_ref + T * R);
     h->c6.assign(t.c6_ref, t.c6_ref + (size_t)T * T * R * R);

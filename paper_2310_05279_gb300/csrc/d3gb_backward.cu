@@ -91,7 +91,7 @@ struct BConsts {
 __global__ void kb_xdot(Work w, BW b, const double* __restrict__ gF, int64_t nt) {
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= nt || q >= w.Nr + w.start_ghost[w.ncells]) return;
-    const int src = __float_as_int(w.hi[q].w) >> 4;
+    const int src = rec_tsrc(w, q) >> 4;
     const int i = w.perm[src];
 #pragma unroll
     for (int a = 0; a < 3; ++a) b.xd[3 * q + a] = gF[3 * (int64_t)i + a] * (1.0 / kBohrA);
@@ -130,7 +130,7 @@ __global__ void kb_weights(Work w, BW b, BConsts c, const double* __restrict__ c
                            const double* __restrict__ c6) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= w.Nr) return;
-    const int t = __float_as_int(w.hi[p].w) & 15;
+    const int t = rec_tsrc(w, p) & 15;
     const Dual n = b.n[p];
     const int nr = nref[t];
     Dual z[R], ex[R], L[R];
@@ -176,7 +176,7 @@ template <int R>
 __global__ void kb_disp(Work w, BW b, BConsts c, const dbl4* __restrict__ pairb) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= w.Nr) return;
-    const int ti = __float_as_int(w.hi[p].w) & 15;
+    const int ti = rec_tsrc(w, p) & 15;
     Dual Wi[R], dWi[R];
 #pragma unroll
     for (int a = 0; a < R; ++a) {
@@ -191,7 +191,7 @@ __global__ void kb_disp(Work w, BW b, BConsts c, const dbl4* __restrict__ pairb)
         Dual d[3], r2;
         ddist(w, b, p, q, d, r2);
         if (!(r2.v < c.rc_disp2)) return;
-        const int tsq = __float_as_int(w.hi[q].w);
+        const int tsq = rec_tsrc(w, q);
         const int src = tsq >> 4;
         const dbl4 pb = pairb[ti * c.T + (tsq & 15)];
         const double R0 = pb.x, Rd = pb.y, R0sq = pb.z;
@@ -239,7 +239,7 @@ __global__ void kb_chain(Work w, BW b, BConsts c, const double* __restrict__ gE,
         Dual d[3], r2;
         ddist(w, b, p, q, d, r2);
         if (!(r2.v < c.rc_cn2)) return;
-        const int src = __float_as_int(w.hi[q].w) >> 4;
+        const int src = rec_tsrc(w, q) >> 4;
         const Dual rinv = inv(dsqrt(r2));
         const double rc = rki + w.pos64[q].w;
         const Dual t = dexp(-c.k1 * (rc * rinv + (-1.0)));

@@ -13,6 +13,8 @@
 //   * per-atom neighbour lists within the two list radii.
 // Every kernel writes only inside the capacities it is given and records an
 // overflow in the status word instead.
+#include <algorithm>
+
 #include "d3gb_internal.cuh"
 
 namespace d3gb {
@@ -42,64 +44,88 @@ __device__ inline int warp_aggregated_inc(int* ctr) {
     return base + rank;
 }
 
-// Wrap, bin, and emit image atoms.  Image slots are reserved once per block:
-// each thread counts its kept images, the block scans the counts in shared
-// memory and one thread reserves the block's range with a single atomic.
-__global__ void __launch_bounds__(256) k_bin(Work w, const double* __restrict__ pos, const int32_t* __restrict__ types) {
+// Wrap into the cell, bin, and record each structure's occupied fractional
+// range per periodic axis (as float bits: the fractions are >= 0).
+__global__ void __launch_bounds__(256) k_wrap(Work w, const double* __restrict__ pos, const int32_t* __restrict__ types) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= w.Nr) return;
+    const int s = struct_of(w.offsets, w.B, i);
+    const StructGeo& G = w.geo[s];
+    double xb[3];
+    bool fin = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        xb[a] = pos[3 * i + a] * (1.0 / kBohrA);
+        fin = fin && isfinite(xb[a]);
+    }
+    if (!fin) {
+        atomicOr(w.status, ST_NONFINITE);
+        xb[0] = xb[1] = xb[2] = 0.0;
+    }
+    const int t = types[i];
+    if (t < 0 || t >= w.T) atomicOr(w.status, ST_TYPE);
+    double f[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        f[k] = xb[0] * G.Hinv[k] + xb[1] * G.Hinv[3 + k] + xb[2] * G.Hinv[6 + k];
+        if (G.pbc[k]) {
+            f[k] -= floor(f[k]);
+            if (f[k] >= 1.0) f[k] -= 1.0;
+        }
+        w.fw[3 * i + k] = f[k];
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) w.xw[3 * i + a] = f[0] * G.H[a] + f[1] * G.H[3 + a] + f[2] * G.H[6 + a];
+    const int cid = cell_id(G, f);
+    w.cell_of[i] = cid;
+    w.slot_of[i] = atomicAdd(&w.cnt_real[cid], 1);
+    // occupied range: one atomic per group of lanes in the same structure
+    const unsigned grp = __match_any_sync(__activemask(), s);
+    const bool leader = (threadIdx.x & 31) == __ffs(grp) - 1;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        if (!G.pbc[k]) continue;
+        const int lo = __reduce_min_sync(grp, __float_as_int(__double2float_rd(f[k])));
+        const int hi = __reduce_max_sync(grp, __float_as_int(__double2float_ru(f[k])));
+        if (leader) {
+            atomicMin(&w.frange[3 * s + k], lo);
+            atomicMax(&w.frange[3 * (w.B + s) + k], hi);
+        }
+    }
+}
+
+// Periodic images that can be within the list radius of a real atom: along a
+// periodic axis an image is kept when its fraction lies within delta (list
+// radius / plane spacing) of the structure's occupied range.  Slots are
+// reserved once per block (each thread counts, the block scans, one atomic).
+__global__ void __launch_bounds__(256) k_images(Work w) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool live = i < w.Nr;
-    int s = 0;
+    const int s = live ? struct_of(w.offsets, w.B, i) : 0;
+    const StructGeo& G = w.geo[s];
     double f[3] = {0, 0, 0};
+    int nlo[3] = {0, 0, 0}, nhi[3] = {0, 0, 0};
+    double u0[3] = {0, 0, 0};
     if (live) {
-        s = struct_of(w.offsets, w.B, i);
-        const StructGeo& G = w.geo[s];
-        double xb[3];
-        bool fin = true;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            xb[a] = pos[3 * i + a] * (1.0 / kBohrA);
-            fin = fin && isfinite(xb[a]);
-        }
-        if (!fin) {
-            atomicOr(w.status, ST_NONFINITE);
-            xb[0] = xb[1] = xb[2] = 0.0;
-        }
-        const int t = types[i];
-        if (t < 0 || t >= w.T) atomicOr(w.status, ST_TYPE);
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            f[k] = xb[0] * G.Hinv[k] + xb[1] * G.Hinv[3 + k] + xb[2] * G.Hinv[6 + k];
-            if (G.pbc[k]) {
-                f[k] -= floor(f[k]);
-                if (f[k] >= 1.0) f[k] -= 1.0;
+            f[k] = w.fw[3 * i + k];
+            u0[k] = (f[k] - G.lo[k]) * G.fscale[k];
+            if (G.img[k] > 0) {
+                const double delta = G.ext_hi[k] - 1.0;
+                const double omin = (double)__int_as_float(w.frange[3 * s + k]);
+                const double omax = (double)__int_as_float(w.frange[3 * (w.B + s) + k]);
+                nlo[k] = max(-G.img[k], (int)ceil(fmax(G.ext_lo[k], omin - delta) - f[k]));
+                nhi[k] = min(G.img[k], min((int)ceil(G.ext_hi[k] - f[k]) - 1, (int)floor(omax + delta - f[k])));
             }
         }
-#pragma unroll
-        for (int a = 0; a < 3; ++a) w.xw[3 * i + a] = f[0] * G.H[a] + f[1] * G.H[3 + a] + f[2] * G.H[6 + a];
-        const int cid = cell_id(G, f);
-        w.cell_of[i] = cid;
-        w.slot_of[i] = atomicAdd(&w.cnt_real[cid], 1);
     }
-    const StructGeo& G = w.geo[s];
-    auto kept = [&](int n0, int n1, int n2, double g[3]) {
-        g[0] = f[0] + n0;
-        g[1] = f[1] + n1;
-        g[2] = f[2] + n2;
-#pragma unroll
-        for (int k = 0; k < 3; ++k)
-            if (G.img[k] > 0 && (g[k] < G.ext_lo[k] || g[k] >= G.ext_hi[k])) return false;
-        return true;
-    };
-    // pass 1: count
     int mine = 0;
-    if (live)
-        for (int n0 = -G.img[0]; n0 <= G.img[0]; ++n0)
-            for (int n1 = -G.img[1]; n1 <= G.img[1]; ++n1)
-                for (int n2 = -G.img[2]; n2 <= G.img[2]; ++n2) {
-                    if (n0 == 0 && n1 == 0 && n2 == 0) continue;
-                    double g[3];
-                    if (kept(n0, n1, n2, g)) ++mine;
-                }
+    if (live && nhi[0] >= nlo[0] && nhi[1] >= nlo[1] && nhi[2] >= nlo[2]) {
+        mine = (nhi[0] - nlo[0] + 1) * (nhi[1] - nlo[1] + 1) * (nhi[2] - nlo[2] + 1);
+        // the identity is always inside the range; it is the atom itself
+        mine -= 1;
+    }
     // block scan of the counts
     __shared__ int wsum[8];
     __shared__ int base;
@@ -122,20 +148,24 @@ __global__ void __launch_bounds__(256) k_bin(Work w, const double* __restrict__ 
         base = acc > 0 ? atomicAdd(w.ghost_count, acc) : 0;
     }
     __syncthreads();
-    if (!live || mine == 0) return;
+    if (!live || mine <= 0) return;
     int slot = base + wsum[wid] + x - mine;
-    // pass 2: write
-    for (int n0 = -G.img[0]; n0 <= G.img[0]; ++n0)
-        for (int n1 = -G.img[1]; n1 <= G.img[1]; ++n1)
-            for (int n2 = -G.img[2]; n2 <= G.img[2]; ++n2) {
+    auto cell_of_axis = [&](int k, int n) {
+        const int c = (int)floor(u0[k] + n * G.fscale[k]);
+        return min(max(c, 0), G.ncell[k] - 1);
+    };
+    for (int n0 = nlo[0]; n0 <= nhi[0]; ++n0) {
+        const int cx = cell_of_axis(0, n0);
+        for (int n1 = nlo[1]; n1 <= nhi[1]; ++n1) {
+            const int cy = cell_of_axis(1, n1);
+            for (int n2 = nlo[2]; n2 <= nhi[2]; ++n2) {
                 if (n0 == 0 && n1 == 0 && n2 == 0) continue;
-                double g[3];
-                if (!kept(n0, n1, n2, g)) continue;
                 if (slot >= w.ghost_cap) {
                     atomicOr(w.status, ST_GHOST_CAP);
                     return;
                 }
-                const int gc = cell_id(G, g);
+                const int cz = cell_of_axis(2, n2);
+                const int gc = (int)(G.cell_base + ((int64_t)cz * G.ncell[1] + cy) * G.ncell[0] + cx);
                 w.ghost_src[slot] = (int)i;
                 w.ghost_shift[slot] = pack_shift(n0, n1, n2);
                 w.ghost_cell[slot] = gc;
@@ -143,6 +173,8 @@ __global__ void __launch_bounds__(256) k_bin(Work w, const double* __restrict__ 
                 w.ghost_sid[slot] = s;
                 ++slot;
             }
+        }
+    }
 }
 
 // ---- exclusive scan of int counts (n entries) into start[0..n], start[n] = total
@@ -266,8 +298,8 @@ __device__ inline void store_pos(Work& w, int64_t q, const double x[3], double r
         h[a] = (float)g;
         l[a] = (float)(x[a] - (double)h[a]);
     }
-    w.hi[q] = make_float4(h[0], h[1], h[2], __int_as_float(tsrc));
-    w.lo[q] = make_float4(l[0], l[1], l[2], (float)rk);
+    w.rec[2 * q] = make_float4(h[0], h[1], h[2], __int_as_float(tsrc));
+    w.rec[2 * q + 1] = make_float4(l[0], l[1], l[2], (float)rk);
 }
 
 __global__ void k_fill_real(Work w, const int32_t* __restrict__ types, const double* __restrict__ rk_tab) {
@@ -301,73 +333,138 @@ __global__ void k_fill_ghost(Work w, const int32_t* __restrict__ types, const do
     store_pos(w, w.Nr + q, x, rk_tab[t], t | (w.slot_of[i] << 4));
 }
 
-// Per-atom lists within the two list radii (FP32 split positions; the list
-// radii carry a relative margin so every pair inside the true cutoff is listed).
-__global__ void k_build_lists(Work w) {
-    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= w.Nr) return;
-    const int s = w.sid[p];
-    const StructGeo& G = w.geo[s];
-    int rel = w.cell_sorted[p] - (int)G.cell_base;
-    const int c0 = rel % G.ncell[0];
-    rel /= G.ncell[0];
-    const int c1 = rel % G.ncell[1];
-    const int c2 = rel / G.ncell[1];
-    const float4 hp = w.hi[p];
-    const int64_t local = p - G.atom_base;
-    int* Ld = w.nbr_disp + list_row(G.list_base_disp, local, G.cap_disp);
-    int* Lc = w.nbr_cn + list_row(G.list_base_cn, local, G.cap_cn);
-    const int capd = G.cap_disp, capc = G.cap_cn;
-    int nd = 0, nc = 0;
+// ---- per-atom lists within the two list radii ------------------------------
+// Positions used here are the grid-aligned hi parts (error <= sqrt(3) 2^-10
+// bohr, covered by the list margin).  Both variants are persistent: each warp
+// repeatedly takes the next 32 consecutive sorted atoms from a global counter,
+// which balances uneven chunks across SMs.
+
+// Shared per-atom state of a list builder lane.
+struct ListLane {
+    int64_t p;
+    bool live;
+    int s, c0, c1, c2;
+    float4 hp;
+    int* Ld;
+    int* Lc;
+    int* bd;  // 8 staged entries of each list (shared memory)
+    int* bc;
+    int capd, capc, nd, nc;
+    __device__ void init(const Work& w, int64_t P, int* stage_d, int* stage_c) {
+        bd = stage_d;
+        bc = stage_c;
+        p = P;
+        live = P < w.Nr;
+        s = live ? w.sid[P] : -1;
+        c0 = c1 = c2 = 0;
+        hp = make_float4(0.f, 0.f, 0.f, 0.f);
+        Ld = Lc = nullptr;
+        capd = capc = nd = nc = 0;
+        if (!live) return;
+        const StructGeo& G = w.geo[s];
+        int rel = w.cell_sorted[P] - (int)G.cell_base;
+        c0 = rel % G.ncell[0];
+        rel /= G.ncell[0];
+        c1 = rel % G.ncell[1];
+        c2 = rel / G.ncell[1];
+        hp = rec_hi(w, P);
+        const int64_t local = P - G.atom_base;
+        Ld = w.nbr_disp + list_row(G.list_base_disp, local, G.cap_disp);
+        Lc = w.nbr_cn + list_row(G.list_base_cn, local, G.cap_cn);
+        capd = G.cap_disp;
+        capc = G.cap_cn;
+    }
+    // stage q; the 8th entry of a group writes the group as one sector (rows
+    // and capacities are multiples of 8 ints, so groups are 32-byte aligned)
+    __device__ __forceinline__ static void push(int* L, int cap, int& n, int* b, int q) {
+        b[n & 7] = q;
+        if ((n & 7) == 7 && n < cap) {
+            int4* dst = reinterpret_cast<int4*>(L + (n - 7));
+            dst[0] = *reinterpret_cast<const int4*>(b);
+            dst[1] = *reinterpret_cast<const int4*>(b + 4);
+        }
+        ++n;
+    }
+    __device__ __forceinline__ static void drain(int* L, int cap, int n, const int* b) {
+        const int base = n & ~7;
+        for (int k = base; k < n; ++k)
+            if (k < cap) L[k] = b[k & 7];
+    }
+    __device__ __forceinline__ void add(int q, float r2, float rd2, float rn2) {
+        if (r2 < rd2 && q != (int)p) {
+            push(Ld, capd, nd, bd, q);
+            if (r2 < rn2) push(Lc, capc, nc, bc, q);
+        }
+    }
+    __device__ void finish(Work& w, int lane) {
+        if (live) {
+            drain(Ld, capd, nd, bd);
+            drain(Lc, capc, nc, bc);
+            w.cnt_disp[p] = min(nd, capd);
+            w.cnt_cn[p] = min(nc, capc);
+            if (nd > capd || nc > capc) atomicOr(w.status, ST_LIST_CAP);
+        }
+        // per-structure maxima (one atomic per group of lanes in the same structure)
+        const unsigned grp = __match_any_sync(0xffffffffu, s);
+        const int md = __reduce_max_sync(grp, nd), mc = __reduce_max_sync(grp, nc);
+        if (live && lane == __ffs(grp) - 1) {
+            atomicMax(&w.maxcnt[2 * s], md);
+            atomicMax(&w.maxcnt[2 * s + 1], mc);
+        }
+    }
+};
+
+__device__ __forceinline__ int64_t next_chunk(const Work& w, int lane) {
+    int chunk = 0;
+    if (lane == 0) chunk = atomicAdd(w.work_ctr, 1);
+    return (int64_t)__shfl_sync(0xffffffffu, chunk, 0) * 32;
+}
+
+// Every thread walks the cell window of its own atom, rows of cells as
+// contiguous index ranges, four candidates loaded per step.  Appends are
+// staged in shared memory, 8 per list, and leave as whole 32-byte sectors.
+__global__ void __launch_bounds__(128) k_build_lists(Work w) {
+    const int lane = threadIdx.x & 31;
     const float rd2 = w.rl_disp2, rn2 = w.rl_cn2;
-    const int z0 = max(0, c2 - G.win[2]), z1 = min(G.ncell[2] - 1, c2 + G.win[2]);
-    const int y0 = max(0, c1 - G.win[1]), y1 = min(G.ncell[1] - 1, c1 + G.win[1]);
-    const int x0 = max(0, c0 - G.win[0]), x1 = min(G.ncell[0] - 1, c0 + G.win[0]);
-    auto test = [&](int64_t q, float4 hq) {
-        // grid-aligned hi parts: error <= sqrt(3) 2^-10 bohr, covered by the list margin
-        const float dx = hq.x - hp.x, dy = hq.y - hp.y, dz = hq.z - hp.z;
-        const float r2 = dx * dx + dy * dy + dz * dz;
-        if (q == p) return;
-        if (r2 < rd2) {
-            if (nd < capd) Ld[list_off(nd)] = (int)q;
-            ++nd;
-        }
-        if (r2 < rn2) {
-            if (nc < capc) Lc[list_off(nc)] = (int)q;
-            ++nc;
-        }
-    };
-    const float4* __restrict__ H = w.hi;
-    for (int z = z0; z <= z1; ++z)
-        for (int y = y0; y <= y1; ++y) {
-            const int64_t row = G.cell_base + ((int64_t)z * G.ncell[1] + y) * G.ncell[0];
-            const int rb = __ldg(&w.start_real[row + x0]), re = __ldg(&w.start_real[row + x1 + 1]);
-            const int gb = __ldg(&w.start_ghost[row + x0]), ge = __ldg(&w.start_ghost[row + x1 + 1]);
-            for (int pass = 0; pass < 2; ++pass) {
-                const int64_t off = pass == 0 ? 0 : w.Nr;
-                const int b = pass == 0 ? rb : gb, e = pass == 0 ? re : ge;
-                int u = b;
-                for (; u + 4 <= e; u += 4) {
-                    const float4 h0 = __ldg(&H[off + u]), h1 = __ldg(&H[off + u + 1]);
-                    const float4 h2 = __ldg(&H[off + u + 2]), h3 = __ldg(&H[off + u + 3]);
-                    test(off + u, h0);
-                    test(off + u + 1, h1);
-                    test(off + u + 2, h2);
-                    test(off + u + 3, h3);
+    const float4* __restrict__ H = w.rec;  // hi parts at even indices
+    __shared__ __align__(16) int stage[2][128][8];
+    for (;;) {
+        const int64_t p0 = next_chunk(w, lane);
+        if (p0 >= w.Nr) return;
+        ListLane L;
+        L.init(w, p0 + lane, stage[0][threadIdx.x], stage[1][threadIdx.x]);
+        if (L.live) {
+            const StructGeo& G = w.geo[L.s];
+            const int x0 = max(0, L.c0 - G.win[0]), x1 = min(G.ncell[0] - 1, L.c0 + G.win[0]);
+            const int y0 = max(0, L.c1 - G.win[1]), y1 = min(G.ncell[1] - 1, L.c1 + G.win[1]);
+            const int z0 = max(0, L.c2 - G.win[2]), z1 = min(G.ncell[2] - 1, L.c2 + G.win[2]);
+            const float4 hp = L.hp;
+            auto test = [&](int q, float4 hq) {
+                const float dx = hq.x - hp.x, dy = hq.y - hp.y, dz = hq.z - hp.z;
+                L.add(q, fmaf(dx, dx, fmaf(dy, dy, dz * dz)), rd2, rn2);
+            };
+            for (int z = z0; z <= z1; ++z)
+                for (int y = y0; y <= y1; ++y) {
+                    const int64_t row = G.cell_base + ((int64_t)z * G.ncell[1] + y) * G.ncell[0];
+                    const int rb = __ldg(&w.start_real[row + x0]), re = __ldg(&w.start_real[row + x1 + 1]);
+                    const int gb = (int)w.Nr + __ldg(&w.start_ghost[row + x0]);
+                    const int ge = (int)w.Nr + __ldg(&w.start_ghost[row + x1 + 1]);
+                    for (int pass = 0; pass < 2; ++pass) {
+                        const int b = pass == 0 ? rb : gb, e = pass == 0 ? re : ge;
+                        int u = b;
+                        for (; u + 4 <= e; u += 4) {
+                            const float4 h0 = __ldg(&H[2 * u]), h1 = __ldg(&H[2 * u + 2]);
+                            const float4 h2 = __ldg(&H[2 * u + 4]), h3 = __ldg(&H[2 * u + 6]);
+                            test(u, h0);
+                            test(u + 1, h1);
+                            test(u + 2, h2);
+                            test(u + 3, h3);
+                        }
+                        for (; u < e; ++u) test(u, __ldg(&H[2 * u]));
+                    }
                 }
-                for (; u < e; ++u) test(off + u, __ldg(&H[off + u]));
-            }
         }
-    w.cnt_disp[p] = min(nd, capd);
-    w.cnt_cn[p] = min(nc, capc);
-    if (nd > capd || nc > capc) atomicOr(w.status, ST_LIST_CAP);
-    // per-structure maxima (one atomic per group of lanes in the same structure)
-    const unsigned mask = __activemask();
-    const unsigned grp = __match_any_sync(mask, s);
-    const int md = __reduce_max_sync(grp, nd), mc = __reduce_max_sync(grp, nc);
-    if ((threadIdx.x & 31) == __ffs(grp) - 1) {
-        atomicMax(&w.maxcnt[2 * s], md);
-        atomicMax(&w.maxcnt[2 * s + 1], mc);
+        L.finish(w, lane);
     }
 }
 
@@ -390,7 +487,8 @@ cudaError_t launch_build_impl(const Work& w, const double* pos, const int32_t* t
                               int* bsum, cudaStream_t st) {
     if (w.Nr == 0) return cudaGetLastError();
     const int TB = 256;
-    k_bin<<<nblk(w.Nr, TB), TB, 0, st>>>(w, pos, types);
+    k_wrap<<<nblk(w.Nr, TB), TB, 0, st>>>(w, pos, types);
+    k_images<<<nblk(w.Nr, TB), TB, 0, st>>>(w);
     cudaError_t e = scan(w.cnt_real, w.start_real, bsum, w.ncells, st);
     if (e != cudaSuccess) return e;
     e = scan(w.cnt_ghost, w.start_ghost, bsum, w.ncells, st);
@@ -400,7 +498,12 @@ cudaError_t launch_build_impl(const Work& w, const double* pos, const int32_t* t
     k_sort_cells<<<nblk(w.ncells, TB), TB, 0, st>>>(w);
     k_fill_real<<<nblk(w.Nr, TB), TB, 0, st>>>(w, types, rk_tab);
     if (w.ghost_cap > 0) k_fill_ghost<<<nblk(w.ghost_cap, TB), TB, 0, st>>>(w, types, rk_tab);
-    k_build_lists<<<nblk(w.Nr, 128), 128, 0, st>>>(w);
+    {
+        // persistent warps: enough blocks to fill every SM, work handed out per 32 atoms
+        const int chunks = (int)((w.Nr + 31) / 32);
+        const int blocks = std::min((chunks + 3) / 4, w.num_sms * 8);
+        k_build_lists<<<blocks, 128, 0, st>>>(w);
+    }
     return cudaGetLastError();
 }
 

@@ -8,13 +8,14 @@
 //                list radius of the cell; stored after the real atoms, sorted
 //                by cell.  Atom index q < Nr is real, q >= Nr is an image.
 //   per atom q   pos64[q] = (x, y, z, k2*Rcov) in bohr, FP64
-//                hi[q], lo[q] = FP32 split of the position (x = hi + lo) with
-//                hi.w = type | (data source << 4) as int bits, lo.w = k2*Rcov
-//   lists        per structure, blocked: atoms in groups of 32 by local index
-//                l = p - atom_base_s; entry k of atom l is at
-//                list_base_s + (l / 32) * cap_s * 32 + (k / 8) * 256 + (l % 32) * 8 + k % 8,
-//                so each lane owns whole 32-byte sectors (8 entries) and a warp
-//                reads 4 entries per lane with one coalesced 16-byte load.
+//                rec[q] = 32-byte record {hi.xyz, tsrc, lo.xyz, k2*Rcov}: the FP32
+//                split of the position (x = hi + lo, hi on a 2^-10 bohr grid),
+//                tsrc = type | (data source << 4) as int bits.  One 256-bit
+//                load fetches the whole record.
+//   lists        per structure, one row of cap_s entries per atom:
+//                entry k of sorted atom p is at list_base_s + (p - atom_base_s) * cap_s + k.
+//                A thread appends to its own row, so every 32-byte sector is
+//                filled by one thread, and reads it 4 entries per 16-byte load.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -85,9 +86,10 @@ struct Work {
     int* sorted_src;         // [Nr] sorted -> input index
     int* gsorted;            // [ghost_cap] sorted image slot -> raw image record
     // per atom, sorted
-    dbl4* pos64;          // [Nr + ghost_cap]
-    float4* hi;              // [Nr + ghost_cap]
-    float4* lo;              // [Nr + ghost_cap]
+    dbl4* pos64;             // [Nr + ghost_cap]
+    float4* rec;             // [2 * (Nr + ghost_cap)]: hi at 2q, lo at 2q + 1
+    double* fw;              // [Nr * 3] wrapped fractional coordinates, input order
+    int* frange;             // [2][B][3] float bits: min and max occupied fraction per axis
     int* perm;               // [Nr] sorted -> input index
     int* sid;                // [Nr] structure of sorted real atom
     int* cell_sorted;        // [Nr] global cell id of sorted real atom
@@ -97,12 +99,14 @@ struct Work {
     int* cnt_disp;           // [Nr]
     int* cnt_cn;             // [Nr]
     int* maxcnt;             // [2*B] max list length per structure (disp, cn)
+    int* work_ctr;           // [1] persistent-kernel work counter (zeroed before each build)
+    int num_sms;
     float rl_disp2, rl_cn2;  // list radii squared, bohr^2
     // passes
     double* cn;              // [Nr]
     void* W;                 // [Nr][RP] real
     void* dW;                // [Nr][RP] real
-    void* v;                 // [Nr][T][RP] real: v_q^(t)_a = sum_b C6ref[t][tq][a][b] W_qb
+    void* v;                 // [Nr][T][RP] real: v_q^(t)_a = sum_b C6ref[t][tq][a][b] W_qb (RP = 4 or 8)
     void* dEdn;              // [Nr] real
     void* Fd;                // [Nr][4] real (direct forces)
     double* eat;             // [Nr] site energies, Ha
@@ -120,16 +124,27 @@ struct Consts {
     int T, R, RP;
 };
 
-// ---- blocked neighbour lists
-__host__ __device__ inline int64_t list_row(int64_t base, int64_t local, int cap) {
-    return base + (local >> 5) * (int64_t)cap * 32 + (local & 31) * 8;
-}
-__host__ __device__ inline int list_off(int k) { return (k >> 3) * 256 + (k & 7); }
+// ---- neighbour lists: one row of `cap` entries per atom (cap a multiple of 8),
+// rows of a structure contiguous; each thread appends to and reads its own row
+__host__ __device__ inline int64_t list_row(int64_t base, int64_t local, int cap) { return base + local * (int64_t)cap; }
+__host__ __device__ inline int list_off(int k) { return k; }
 __host__ __device__ inline int round_cap(double c) {
     int v = (int)c;
     return (v + 7) & ~7;
 }
-__host__ __device__ inline int64_t list_size(int64_t natoms, int cap) { return ((natoms + 31) >> 5) * 32 * (int64_t)cap; }
+__host__ __device__ inline int64_t list_size(int64_t natoms, int cap) { return natoms * (int64_t)cap; }
+
+// 256-bit read-only load (sm_100 and later)
+__device__ __forceinline__ void ld8(const float* p, float4& a, float4& b) {
+    asm volatile("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+                 : "l"(p));
+}
+__device__ __forceinline__ void rec_load(const Work& w, int64_t q, float4& hi, float4& lo) {
+    ld8(reinterpret_cast<const float*>(w.rec + 2 * q), hi, lo);
+}
+__device__ __forceinline__ float4 rec_hi(const Work& w, int64_t q) { return __ldg(w.rec + 2 * q); }
+__device__ __forceinline__ int rec_tsrc(const Work& w, int64_t q) { return __float_as_int(__ldg(&w.rec[2 * q].w)); }
 
 struct ListView {
     const int* p;  // the atom's row (list_row)
@@ -184,5 +199,5 @@ struct Tabs {
 cudaError_t launch_forward(const Work& w, const Consts& c, bool mixed, const Tabs& tabs, double* E, double* F,
                            double* W, double* e_atom, double* cn_out, int B, cudaStream_t st, cudaEvent_t* marks);
 constexpr int kForwardLaunches = 6;  // kernels per forward pass (B > 0, N > 0)
-constexpr int kBuildLaunches = 12;   // kernels per neighbour build (N > 0, with images)
+constexpr int kBuildLaunches = 13;   // kernels per neighbour build (N > 0, with images)
 }  // namespace d3gb

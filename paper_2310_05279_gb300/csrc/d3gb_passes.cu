@@ -76,12 +76,13 @@ template <> struct Site<true> {
     float4 h, l;
     const Work* w;
     int64_t p;
-    __device__ Site(const Work& W, int64_t P) : w(&W), p(P) { h = W.hi[P]; l = W.lo[P]; }
+    __device__ Site(const Work& W, int64_t P) : w(&W), p(P) { rec_load(W, P, h, l); }
     __device__ int tsrc() const { return __float_as_int(h.w); }
     __device__ float rk() const { return l.w; }
     // distance vector to q; returns the neighbour's packed type/source and k2*Rcov
     __device__ void dist(int q, float& dx, float& dy, float& dz, float& r2, int& tq, float& rkq) const {
-        const float4 hq = w->hi[q], lq = w->lo[q];
+        float4 hq, lq;
+        rec_load(*w, q, hq, lq);
         dx = (hq.x - h.x) + (lq.x - l.x);
         dy = (hq.y - h.y) + (lq.y - l.y);
         dz = (hq.z - h.z) + (lq.z - l.z);
@@ -91,7 +92,8 @@ template <> struct Site<true> {
     }
     // exact pair vector as D + e (hi parts lie on a common grid, so hq - hp is exact)
     __device__ void dist_exact(int q, float (&D)[3], float (&e)[3], int& tq) const {
-        const float4 hq = w->hi[q], lq = w->lo[q];
+        float4 hq, lq;
+        rec_load(*w, q, hq, lq);
         const float A[3] = {hq.x - h.x, hq.y - h.y, hq.z - h.z};
         const float Bv[3] = {lq.x - l.x, lq.y - l.y, lq.z - l.z};
 #pragma unroll
@@ -114,7 +116,7 @@ template <> struct Site<false> {
     dbl4 x;
     int ts;
     const Work* w;
-    __device__ Site(const Work& W, int64_t P) : w(&W) { x = W.pos64[P]; ts = __float_as_int(W.hi[P].w); }
+    __device__ Site(const Work& W, int64_t P) : w(&W) { x = W.pos64[P]; ts = rec_tsrc(W, P); }
     __device__ int tsrc() const { return ts; }
     __device__ double rk() const { return x.w; }
     __device__ void dist(int q, double& dx, double& dy, double& dz, double& r2, int& tq, double& rkq) const {
@@ -123,7 +125,7 @@ template <> struct Site<false> {
         dy = y.y - x.y;
         dz = y.z - x.z;
         r2 = dx * dx + dy * dy + dz * dz;
-        tq = __float_as_int(w->hi[q].w);
+        tq = rec_tsrc(*w, q);
         rkq = y.w;
     }
     __device__ bool inside(int, double r2, double rc2, double) const { return r2 < rc2; }
@@ -151,15 +153,20 @@ __device__ __forceinline__ void load_vec(const T* __restrict__ p, T (&x)[R]) {
 #pragma unroll
     for (int a = 0; a < R; ++a) x[a] = p[a];
 }
+// p is 16-byte aligned for R <= 4 and 32-byte aligned (one 256-bit load) for R <= 8
 template <int R>
 __device__ __forceinline__ void load_vec(const float* __restrict__ p, float (&x)[R]) {
+    if constexpr (R <= 4) {
+        const float4 t = __ldg(reinterpret_cast<const float4*>(p));
+        const float tv[4] = {t.x, t.y, t.z, t.w};
 #pragma unroll
-    for (int a = 0; a < R; a += 4) {
-        const float4 t = __ldg(reinterpret_cast<const float4*>(p + a));
-        x[a] = t.x;
-        if (a + 1 < R) x[a + 1] = t.y;
-        if (a + 2 < R) x[a + 2] = t.z;
-        if (a + 3 < R) x[a + 3] = t.w;
+        for (int a = 0; a < R; ++a) x[a] = tv[a];
+    } else {
+        float4 t0, t1;
+        ld8(p, t0, t1);
+        const float tv[8] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w};
+#pragma unroll
+        for (int a = 0; a < R; ++a) x[a] = tv[a];
     }
 }
 
@@ -268,7 +275,7 @@ __global__ void __launch_bounds__(128) k_weights(Work w, Consts c, const double*
     using T = typename Real<MIXED>::T;
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= w.Nr) return;
-    const int t = __float_as_int(w.hi[p].w) & 15;
+    const int t = rec_tsrc(w, p) & 15;
     const double n = w.cn[p];
     const int nr = nref[t];
     double x[R];

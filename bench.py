@@ -60,51 +60,68 @@ def measured_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clock and throttle-reason samples during the timed region."""
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+    """nvidia-smi clock and throttle-reason samples (every 10 ms), each stamped
+    on arrival; only samples between mark_start() and mark_stop() are kept."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
 
     def __init__(self, gpu_index: int):
         self.idx = gpu_index
         self.p = None
-        self.path = os.path.join("/tmp", f"d3gb_clocks_{os.getpid()}.csv")
+        self.lines = []
+        self.t0 = self.t1 = None
 
     def start(self):
+        import threading
         try:
-            self.f = open(self.path, "w")
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
-                                      stderr=subprocess.DEVNULL)
+                                       "--format=csv,noheader,nounits", "-lms", "10"], stdout=subprocess.PIPE,
+                                      stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.p = None
+            return
+
+        def reader():
+            for line in self.p.stdout:
+                self.lines.append((time.time(), line))
+        self.th = threading.Thread(target=reader, daemon=True)
+        self.th.start()
+        time.sleep(0.3)  # let the sampler start before the timed region
+
+    def mark_start(self):
+        self.t0 = time.time()
+
+    def mark_stop(self):
+        self.t1 = time.time()
 
     def stop(self) -> dict:
         if self.p is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        time.sleep(0.05)
         self.p.terminate()
         try:
             self.p.wait(timeout=5)
         except Exception:
             self.p.kill()
-        self.f.close()
-        sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
+        sm, smax, reasons = [], [], set()
+        for t, line in self.lines:
+            if self.t0 is not None and not (self.t0 <= t <= self.t1 + 0.02):
+                continue
             parts = [x.strip() for x in line.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 7:
                 continue
             try:
-                sm.append(float(parts[1]))
-                smax.append(float(parts[2]))
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
             except ValueError:
                 continue
-            for n, v in zip(names, parts[5:9]):
+            for n, v in zip(names, parts[3:7]):
                 if v.lower() == "active":
                     reasons.add(n)
-        os.unlink(self.path)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "sample_period_ms": 10}
 
 
 def time_steps(torch, fn, steps, warmup, flush=None, stream=None):
@@ -254,8 +271,10 @@ def main():
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
+    clk.mark_start()
     times = time_steps(torch, step, args.steps, 0, flush=flush, stream=stream)
     torch.cuda.synchronize()
+    clk.mark_stop()
     if world > 1:
         torch.distributed.barrier()
     clocks = clk.stop()

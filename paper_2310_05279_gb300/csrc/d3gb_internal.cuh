@@ -136,7 +136,7 @@ __host__ __device__ inline int64_t list_size(int64_t natoms, int cap) { return n
 
 // 256-bit read-only load (sm_100 and later)
 __device__ __forceinline__ void ld8(const float* p, float4& a, float4& b) {
-    asm volatile("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+    asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                  : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
                  : "l"(p));
 }

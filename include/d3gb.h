@@ -175,6 +175,25 @@ d3_status d3_profile_read(d3_handle *h, double *ms, int64_t *calls, int64_t *lau
 /* Zero the stage totals and the launch counter. */
 d3_status d3_profile_reset(d3_handle *h);
 
+/* Per-structure energies from site energies, for callers that cannot allocate
+ * device memory (for example code running while a stream is being captured
+ * into a CUDA graph, or a host program that keeps all device memory in its own
+ * pool).  The paper has no counterpart: this is a service entry point.
+ *  B        number of structures, 0 <= B <= 16384
+ *  offsets  host int64[B+1], offsets[0] = 0, non-decreasing
+ *  e_atom   device double[offsets[B]] site energies (e.g. from d3_compute_batch_ex), eV
+ *  E        device double[B] receives the per-structure sums, eV
+ * Allocates nothing: its scratch is a fixed array of about 0.7 MB inside the
+ * library that every device which loads the library holds until the process
+ * exits.  Limit: B times ceil(largest structure / 4096) must not exceed 65536;
+ * beyond that (or B > 16384) it returns D3_ERR_CAPACITY.  The first call on a
+ * device looks up the array's device address; make that first call before any
+ * stream capture.  All calls share the array, so calls that overlap on the GPU
+ * race; calls ordered on one stream are safe.  Enqueued on `stream`, no
+ * synchronisation, no handle needed. */
+d3_status d3_structure_energies_noalloc(int32_t B, const int64_t *offsets, const double *e_atom, double *E,
+                                        void *stream);
+
 /* Library version string. */
 const char *d3_version(void);
 

@@ -46,6 +46,7 @@ SIGNATURES = {
     "d3_profile_enable": (C.c_int, [_vp, C.c_int32]),
     "d3_profile_read": (C.c_int, [_vp, _dp, _lp, _lp]),
     "d3_profile_reset": (C.c_int, [_vp]),
+    "d3_structure_energies_noalloc": (C.c_int, [C.c_int32, _lp, _vp, _vp, _vp]),
 }
 
 _lib = None

@@ -306,6 +306,7 @@ d3_status plan_alloc(d3_handle* h, Plan& P) {
     A(w.gsorted, int, Ng);
     A(w.pos64, dbl4, Nt);
     A(w.rec, float4, 2 * Nt);
+    A(w.hi, float4, Nt);
     A(w.fw, double, 3 * Nr);
     A(w.frange, int, 6 * (int64_t)B);
     A(w.perm, int, Nr);

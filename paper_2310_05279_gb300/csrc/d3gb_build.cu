@@ -300,6 +300,7 @@ __device__ inline void store_pos(Work& w, int64_t q, const double x[3], double r
     }
     w.rec[2 * q] = make_float4(h[0], h[1], h[2], __int_as_float(tsrc));
     w.rec[2 * q + 1] = make_float4(l[0], l[1], l[2], (float)rk);
+    w.hi[q] = make_float4(h[0], h[1], h[2], 0.f);
 }
 
 __global__ void k_fill_real(Work w, const int32_t* __restrict__ types, const double* __restrict__ rk_tab) {
@@ -426,7 +427,7 @@ __device__ __forceinline__ int64_t next_chunk(const Work& w, int lane) {
 __global__ void __launch_bounds__(128) k_build_lists(Work w) {
     const int lane = threadIdx.x & 31;
     const float rd2 = w.rl_disp2, rn2 = w.rl_cn2;
-    const float4* __restrict__ H = w.rec;  // hi parts at even indices
+    const float4* __restrict__ H = w.hi;
     __shared__ __align__(16) int stage[2][128][8];
     for (;;) {
         const int64_t p0 = next_chunk(w, lane);
@@ -453,14 +454,14 @@ __global__ void __launch_bounds__(128) k_build_lists(Work w) {
                         const int b = pass == 0 ? rb : gb, e = pass == 0 ? re : ge;
                         int u = b;
                         for (; u + 4 <= e; u += 4) {
-                            const float4 h0 = __ldg(&H[2 * u]), h1 = __ldg(&H[2 * u + 2]);
-                            const float4 h2 = __ldg(&H[2 * u + 4]), h3 = __ldg(&H[2 * u + 6]);
+                            const float4 h0 = __ldg(&H[u]), h1 = __ldg(&H[u + 1]);
+                            const float4 h2 = __ldg(&H[u + 2]), h3 = __ldg(&H[u + 3]);
                             test(u, h0);
                             test(u + 1, h1);
                             test(u + 2, h2);
                             test(u + 3, h3);
                         }
-                        for (; u < e; ++u) test(u, __ldg(&H[2 * u]));
+                        for (; u < e; ++u) test(u, __ldg(&H[u]));
                     }
                 }
         }

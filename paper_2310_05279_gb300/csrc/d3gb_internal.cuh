@@ -88,6 +88,7 @@ struct Work {
     // per atom, sorted
     dbl4* pos64;             // [Nr + ghost_cap]
     float4* rec;             // [2 * (Nr + ghost_cap)]: hi at 2q, lo at 2q + 1
+    float4* hi;              // [Nr + ghost_cap] compact copy of the hi parts for the list build
     double* fw;              // [Nr * 3] wrapped fractional coordinates, input order
     int* frange;             // [2][B][3] float bits: min and max occupied fraction per axis
     int* perm;               // [Nr] sorted -> input index

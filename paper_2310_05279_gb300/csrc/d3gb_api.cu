@@ -83,6 +83,7 @@ struct d3_handle {
     dbl4* d_paird = nullptr;
     dbl4* d_pairb = nullptr;  // (R0, R, R0^2, 0) per element pair, for the backward
     float4* d_rcpair = nullptr;  // k2 (Rcov_i + Rcov_j) and its square, FP32 hi + lo
+    float2* d_exptab = nullptr;  // 2^(j/64), j = 0..63, FP32 hi + lo
     double* d_rk = nullptr;
     int* d_status = nullptr;
     cudaStream_t last_stream = nullptr;
@@ -479,6 +480,7 @@ d3_status forward(d3_handle* h, int32_t B, const int64_t* offsets, const double*
     tb.cnref = h->d_cnref;
     tb.nref = h->d_nref;
     tb.rcpair = h->d_rcpair;
+    tb.exptab = h->d_exptab;
     cudaError_t e = launch_forward(P.w, c, mixed, tb, E, F, W, e_atom, cn, B, st,
                                    ev.size() == 7 ? ev.data() + 1 : nullptr);
     if (e != cudaSuccess) return cuda_fail(h, e, "forward launch");
@@ -550,6 +552,7 @@ d3_status d3_create(const d3_params* params, const d3_tables* tables, d3_handle*
     if (e == cudaSuccess) e = m.alloc(&h->d_paird, T * T);
     if (e == cudaSuccess) e = m.alloc(&h->d_pairb, T * T);
     if (e == cudaSuccess) e = m.alloc(&h->d_rcpair, T * T);
+    if (e == cudaSuccess) e = m.alloc(&h->d_exptab, 64);
     if (e == cudaSuccess) e = m.alloc(&h->d_rk, T);
     if (e == cudaSuccess) e = m.alloc(&h->d_status, 1);
     if (e == cudaSuccess) e = cudaMemcpy(h->d_nref, h->nref.data(), T * sizeof(int), cudaMemcpyHostToDevice);
@@ -567,6 +570,13 @@ d3_status d3_create(const d3_params* params, const d3_tables* tables, d3_handle*
             rcp[a2 * T + b2] = make_float4(rh, rl, qh, ql);
         }
     if (e == cudaSuccess) e = cudaMemcpy(h->d_rcpair, rcp.data(), rcp.size() * sizeof(float4), cudaMemcpyHostToDevice);
+    std::vector<float2> ex2(64);
+    for (int j = 0; j < 64; ++j) {
+        const double v = std::exp2(j / 64.0);
+        const float hi = (float)v;
+        ex2[j] = make_float2(hi, (float)(v - (double)hi));
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(h->d_exptab, ex2.data(), ex2.size() * sizeof(float2), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(h->d_status, 0, sizeof(int));
     if (e != cudaSuccess) {
         h->tabmem.release();

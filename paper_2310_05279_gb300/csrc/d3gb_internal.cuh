@@ -193,6 +193,7 @@ struct Tabs {
     const double* cnref;   // [T][R]
     const int* nref;       // [T]
     const float4* rcpair;  // [T][T] k2 (Rcov_i + Rcov_j) as hi, lo and its square as hi, lo (bohr)
+    const float2* exptab;  // [64] 2^(j/64) as FP32 hi, lo
 };
 
 // marks (optional): 6 events recorded before the CN pass and after the CN,

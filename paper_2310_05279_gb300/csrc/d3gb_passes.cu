@@ -179,7 +179,8 @@ __device__ __forceinline__ void load_vec(const float* __restrict__ p, float (&x)
 // expf itself.  Returns false when the pair is outside R_cn.
 __device__ __forceinline__ bool cn_pair_precise(const Site<true>& S, int q, const float4* rrow, float k1, float rc2,
                                                 double rc2d, float (&D)[3], float& r2, float& ah, float& al,
-                                                float& rch, int& tq) {
+                                                float& rch, int& tq, float* rcl_out = nullptr,
+                                                float* r2l_out = nullptr) {
     float e[3];
     S.dist_exact(q, D, e, tq);
     float P[3], pl[3];
@@ -209,9 +210,84 @@ __device__ __forceinline__ bool cn_pair_precise(const Site<true>& S, int q, cons
     const float qh = uh * idh;
     const float ql = (fmaf(-qh, dh, uh) + ul - qh * dl) * idh;
     ah = k1 * qh;
-    al = k1 * ql;
+    al = fmaf(k1, qh, -ah) + k1 * ql;
     rch = rc.x;
+    if (rcl_out) *rcl_out = rc.y;
+    if (r2l_out) *r2l_out = Sl;
     return true;
+}
+
+// ------------------------------------------------------------------ Eq. 4 in double-single
+// t = exp(-a), f = 1/(1 + t) and 1 - f = t f for a = ah + al, each as a
+// double-single pair with a relative error near 1e-11.  The coordination number
+// and its chain-rule forces are sums of many such terms; FP32 rounding of each
+// would leave a small systematic error that the sums accumulate, so the terms
+// are formed here from FP32 operations with error-free transformations.
+//
+// exp follows the table-driven method of P. T. P. Tang (ACM TOMS 15(2), 1989):
+// x = (64 m + j) L + r with L = ln2/64 (carried in three FP32 parts so that the
+// reduction is exact to ~1e-14), exp(x) = 2^m 2^(j/64) exp(r), |r| <= L/2, and
+// exp(r) = 1 + r + r^2/2 + r^3/6 + r^4/24 (truncation below 4e-14).  The table
+// holds 2^(j/64) as FP32 hi + lo pairs.
+constexpr double kLnTwoOver64 = 0.693147180559945309417232121458 / 64.0;
+constexpr float kExpL1 = 1420.0f / 131072.0f;  // 11 significant bits: k L1 is exact for |k| < 2^13
+constexpr float kExpL2 = (float)(kLnTwoOver64 - (double)kExpL1);
+constexpr float kExpL3 = (float)((kLnTwoOver64 - (double)kExpL1) - (double)kExpL2);
+constexpr float kExpInvL = (float)(64.0 / 0.693147180559945309417232121458);
+
+struct CnDS {
+    float th, tl;  // t = exp(-a)
+    float fh, fl;  // f = 1 / (1 + t)
+    float ch, cl;  // 1 - f = t f
+};
+
+__device__ __forceinline__ CnDS cn_ds(float ah, float al, const float2* __restrict__ tab) {
+    // x = -a, clamped so that 2^m stays a normal FP32 scale (|x| <= 87: t in [1.6e-38, 6e37])
+    float xh = -ah, xl = -al;
+    if (fabsf(xh) > 87.0f) { xh = copysignf(87.0f, xh); xl = 0.0f; }
+    const float kf = rintf(xh * kExpInvL);
+    const int k = (int)kf;
+    const float r1 = fmaf(-kf, kExpL1, xh);  // exact (see kExpL1)
+    const float p2 = kf * kExpL2, p2e = fmaf(kf, kExpL2, -p2);
+    float rh, re;
+    two_sum(r1, -p2, rh, re);
+    const float rl = ((re - p2e) - kf * kExpL3) + xl;
+    // exp(r) - 1 = rh + s
+    const float s = rl + rh * rl + rh * rh * fmaf(rh, fmaf(rh, 1.0f / 24.0f, 1.0f / 6.0f), 0.5f);
+    const int j = k & 63, m = (k - j) / 64;
+    const float2 T = __ldg(tab + j);
+    const float ph = T.x * rh, pe = fmaf(T.x, rh, -ph);
+    const float hh = T.x + ph, he = ph - (hh - T.x);  // |T.x| >= |ph|: Fast2Sum
+    const float lo = he + pe + T.y + fmaf(T.x, s, T.y * rh);
+    float th = hh + lo;
+    float tl = lo - (th - hh);
+    th = ldexpf(th, m);
+    tl = ldexpf(tl, m);
+    CnDS o;
+    o.th = th;
+    o.tl = tl;
+    // f = 1/(1 + t) with one residual correction
+    float dh, de;
+    two_sum(1.0f, th, dh, de);
+    const float dl = de + tl;
+    const float y = rcp_nr(dh);
+    const float rho = fmaf(-dh, y, 1.0f) - dl * y;
+    o.fh = y;
+    o.fl = y * rho;
+    // 1 - f = t f
+    const float ch = th * o.fh;
+    o.ch = ch;
+    o.cl = fmaf(th, o.fh, -ch) + fmaf(th, o.fl, tl * o.fh);
+    return o;
+}
+
+// double-single product (ah + al)(bh + bl), result as hi + lo
+__device__ __forceinline__ void ds_mul(float ah, float al, float bh, float bl, float& h, float& l) {
+    const float p = ah * bh;
+    const float e = fmaf(ah, bh, -p);
+    l = fmaf(ah, bl, fmaf(al, bh, e));
+    h = p + l;
+    l = l - (h - p);
 }
 
 // ------------------------------------------------------------------ Eq. 4
@@ -221,7 +297,8 @@ __device__ __forceinline__ bool cn_pair_precise(const Site<true>& S, int q, cons
 // k1 (rc^2 - r^2) / (r (rc + r)) so its error is relative to its own size,
 // and the sum over neighbours is compensated.
 template <bool MIXED>
-__global__ void __launch_bounds__(128) k_cn(Work w, Consts c, const float4* __restrict__ rcpair) {
+__global__ void __launch_bounds__(128) k_cn(Work w, Consts c, const float4* __restrict__ rcpair,
+                                           const float2* __restrict__ exptab) {
     using T = typename Real<MIXED>::T;
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= w.Nr) return;
@@ -238,13 +315,14 @@ __global__ void __launch_bounds__(128) k_cn(Work w, Consts c, const float4* __re
             float D[3], r2, ah, al, rch;
             int tq;
             if (!cn_pair_precise(S, q, rrow, k1, rc2, c.rc_cn2, D, r2, ah, al, rch, tq)) return;
-            const float t = expf(-ah) * (1.0f - al);
-            const float f = rcp_nr(1.0f + t);
-            if (t < 1.0f) {
+            const CnDS z = cn_ds(ah, al, exptab);
+            if (z.th < 1.0f) {
                 ++nint;
-                acc_add(nh, nl, -(t * f));
+                acc_add(nh, nl, -z.ch);
+                nl -= z.cl;
             } else {
-                acc_add(nh, nl, f);
+                acc_add(nh, nl, z.fh);
+                nl += z.fl;
             }
         });
         w.cn[p] = (double)nint + (double)nh + (double)nl;
@@ -403,10 +481,16 @@ __global__ void __launch_bounds__(128) k_disp(Work w, Consts c, const typename R
 }
 
 // ------------------------------------------------------------------ CN chain rule
+// The chain-rule virial is accumulated per atom as -dE/dn_i sum_q f'(r) d(x)d/r
+// (ordered pairs; equal to the symmetric form), whose diagonal terms all have
+// one sign, so the cancellation between atoms and against the dispersion part
+// happens in FP64 (per-atom sums and the per-structure reduction).  The force
+// coefficient (dE/dn_i + dE/dn_q) f'(r)/r uses the double-single argument, the
+// exact rc and 1/r from the double-single r^2.
 template <bool MIXED>
 __global__ void __launch_bounds__(128) k_chain(Work w, Consts c, const float4* __restrict__ rcpair,
-                                              double* __restrict__ F, double* __restrict__ e_atom,
-                                              double* __restrict__ cn_out) {
+                                              const float2* __restrict__ exptab, double* __restrict__ F,
+                                              double* __restrict__ e_atom, double* __restrict__ cn_out) {
     using T = typename Real<MIXED>::T;
     using T4 = typename Real<MIXED>::T4;
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -424,17 +508,28 @@ __global__ void __launch_bounds__(128) k_chain(Work w, Consts c, const float4* _
         const int k1e = min(cnt, k0 + kChunk);
         T sxx = 0, syy = 0, szz = 0, sxy = 0, sxz = 0, syz = 0;
         LV.for_each(k0, k1e, [&](int q) {
-            T dx, dy, dz, coef;
+            T dx, dy, dz, g, dnq;
             if constexpr (MIXED) {
-                float D[3], r2, ah, al, rch;
+                float D[3], r2, ah, al, rch, rcl, r2l;
                 int tq;
-                if (!cn_pair_precise(S, q, rcpair + (S.tsrc() & 15) * c.T, k1, rc2, c.rc_cn2, D, r2, ah, al, rch, tq))
+                if (!cn_pair_precise(S, q, rcpair + (S.tsrc() & 15) * c.T, k1, rc2, c.rc_cn2, D, r2, ah, al, rch, tq,
+                                     &rcl, &r2l))
                     return;
-                const float t = expf(-ah) * (1.0f - al);
-                const float f = rcp_nr(1.0f + t);
-                const float rinv = rsqrt_nr(r2);
-                const float dfdr = -k1 * rch * rinv * rinv * t * f * f;
-                coef = (dni + dEdn[tq >> 4]) * dfdr * rinv;
+                const CnDS z = cn_ds(ah, al, exptab);
+                // 1/r from r^2 = r2 + r2l with one residual step (double-single)
+                const float y0 = rsqrt_nr(r2);
+                const float y2 = y0 * y0, y2e = fmaf(y0, y0, -y2);
+                const float ry = fmaf(-r2, y2, 1.0f) - fmaf(r2, y2e, r2l * y2);
+                const float yh = y0, yl = 0.5f * y0 * ry;
+                // f'(r)/r = -k1 rc f (1 - f) / r^3, formed in double-single and rounded once
+                float a2h, a2l, a3h, a3l, cfh, cfl, uh, ul, gh, gl;
+                ds_mul(yh, yl, yh, yl, a2h, a2l);
+                ds_mul(a2h, a2l, yh, yl, a3h, a3l);
+                ds_mul(z.ch, z.cl, z.fh, z.fl, cfh, cfl);
+                ds_mul(rch, rcl, cfh, cfl, uh, ul);
+                ds_mul(uh, ul, a3h, a3l, gh, gl);
+                g = -k1 * (gh + gl);
+                dnq = dEdn[tq >> 4];
                 dx = D[0]; dy = D[1]; dz = D[2];
             } else {
                 T r2, rkq;
@@ -444,12 +539,15 @@ __global__ void __launch_bounds__(128) k_chain(Work w, Consts c, const float4* _
                 const T rinv = inv_sqrt(r2);
                 T f, dfdr;
                 cn_fun(rinv, S.rk() + rkq, (T)0, k1, f, &dfdr);
-                coef = (dni + dEdn[tsq >> 4]) * dfdr * rinv;
+                g = dfdr * rinv;
+                dnq = dEdn[tsq >> 4];
             }
-            const T tx = coef * dx, ty = coef * dy, tz = coef * dz;
-            fx += tx; fy += ty; fz += tz;
-            sxx = fma(tx, dx, sxx); syy = fma(ty, dy, syy); szz = fma(tz, dz, szz);
-            sxy = fma(tx, dy, sxy); sxz = fma(tx, dz, sxz); syz = fma(ty, dz, syz);
+            const T coef = (dni + dnq) * g;
+            fx += coef * dx; fy += coef * dy; fz += coef * dz;
+            // per-atom geometric sum for the virial (scaled by dE/dn_i below)
+            const T gx = g * dx, gy = g * dy, gz = g * dz;
+            sxx = fma(gx, dx, sxx); syy = fma(gy, dy, syy); szz = fma(gz, dz, szz);
+            sxy = fma(gx, dy, sxy); sxz = fma(gx, dz, sxz); syz = fma(gy, dz, syz);
         });
         Sxx += (double)sxx; Syy += (double)syy; Szz += (double)szz;
         Sxy += (double)sxy; Sxz += (double)sxz; Syz += (double)syz;
@@ -460,9 +558,11 @@ __global__ void __launch_bounds__(128) k_chain(Work w, Consts c, const float4* _
     F[3 * (int64_t)i + 0] = ((double)fd.x + (double)fx) * u;
     F[3 * (int64_t)i + 1] = ((double)fd.y + (double)fy) * u;
     F[3 * (int64_t)i + 2] = ((double)fd.z + (double)fz) * u;
+    // W -= sum over ordered pairs of dE/dn_i f'(r) d(x)d/r
+    const double dn = (double)dni;
     double* wv = w.wv + 6 * p;
-    wv[0] -= 0.5 * Sxx; wv[1] -= 0.5 * Syy; wv[2] -= 0.5 * Szz;
-    wv[3] -= 0.5 * Sxy; wv[4] -= 0.5 * Sxz; wv[5] -= 0.5 * Syz;
+    wv[0] -= dn * Sxx; wv[1] -= dn * Syy; wv[2] -= dn * Szz;
+    wv[3] -= dn * Sxy; wv[4] -= dn * Sxz; wv[5] -= dn * Syz;
     if (e_atom) e_atom[i] = w.eat[p] * kHartreeEV;
     if (cn_out) cn_out[i] = w.cn[p];
 }
@@ -527,13 +627,13 @@ cudaError_t forward_impl(const Work& w, const Consts& c, const Tabs& tb, double*
         if (marks) cudaEventRecord(marks[k], st);
     };
     mark(0);
-    if (w.Nr > 0) k_cn<MIXED><<<nblk(w.Nr, TB), TB, 0, st>>>(w, c, tb.rcpair);
+    if (w.Nr > 0) k_cn<MIXED><<<nblk(w.Nr, TB), TB, 0, st>>>(w, c, tb.rcpair, tb.exptab);
     mark(1);
     if (w.Nr > 0) k_weights<MIXED, R><<<nblk(w.Nr, TB), TB, 0, st>>>(w, c, tb.cnref, tb.nref, (const T*)tb.c6);
     mark(2);
     if (w.Nr > 0) k_disp<MIXED, R><<<nblk(w.Nr, TB), TB, c.T * c.T * sizeof(T4), st>>>(w, c, (const T4*)tb.pair);
     mark(3);
-    if (w.Nr > 0) k_chain<MIXED><<<nblk(w.Nr, TB), TB, 0, st>>>(w, c, tb.rcpair, F, e_atom, cn_out);
+    if (w.Nr > 0) k_chain<MIXED><<<nblk(w.Nr, TB), TB, 0, st>>>(w, c, tb.rcpair, tb.exptab, F, e_atom, cn_out);
     mark(4);
     if (B > 0) {
         const int nchunk = (int)((w.max_natoms + kFinChunk - 1) / kFinChunk);

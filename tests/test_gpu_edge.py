@@ -1,0 +1,156 @@
+"""Edge cases and error reporting through the C ABI: empty inputs, structures
+with no atoms, cells smaller than the cutoff, open and slab boundaries, invalid
+inputs reported as status codes (never faults), capacity regrowth, and CUDA
+graph capture of a compute call."""
+import numpy as np
+import pytest
+
+from paper_2310_05279_gb300 import workloads as wl
+
+from ._helpers import assert_fp64_ok, assert_mixed_ok, to_dev
+
+pytestmark = pytest.mark.gpu
+PRM = dict(wl.PBE_BJ)
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    return torch
+
+
+def handle(tables, precision="mixed"):
+    from paper_2310_05279_gb300 import D3
+    return D3(tables, precision=precision)
+
+
+def test_empty_batch(torch_cuda):
+    d3 = handle(wl.carbon_table())
+    pos = torch_cuda.zeros((0, 3), dtype=torch_cuda.float64, device="cuda")
+    typ = torch_cuda.zeros(0, dtype=torch_cuda.int32, device="cuda")
+    out = d3.compute_batch(pos, typ, [0], np.zeros((0, 9)), np.zeros((0, 3), np.int32))
+    d3.sync_status()
+    assert out["E"].numel() == 0 and out["F"].numel() == 0
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_empty_structures_and_small_cells(torch_cuda, oracle_mod, precision):
+    tabs = wl.random_tables(["H", "C", "O"], 5)
+    g = np.random.Generator(np.random.PCG64(4))
+    structs = [
+        (np.zeros((0, 3)), np.zeros(0, np.int32), np.eye(3) * 10.0, np.ones(3, np.int32)),      # no atoms
+        (np.array([[0.3, 0.2, 0.1]]), np.array([1], np.int32), np.diag([3.1, 3.3, 3.7]), np.ones(3, np.int32)),
+        (g.uniform(0, 4, (5, 3)), g.integers(0, 3, 5).astype(np.int32),
+         np.array([[4.0, 0, 0], [1.1, 3.9, 0], [-0.6, 0.8, 4.3]]), np.ones(3, np.int32)),  # triclinic, tiny
+        (np.zeros((0, 3)), np.zeros(0, np.int32), np.eye(3) * 7.0, np.ones(3, np.int32)),       # no atoms
+        (g.uniform(0, 9, (12, 3)), g.integers(0, 3, 12).astype(np.int32), np.eye(3) * 9.0,
+         np.array([1, 1, 0], np.int32)),                                                          # slab
+        (g.uniform(0, 6, (7, 3)), g.integers(0, 3, 7).astype(np.int32), np.eye(3) * 6.0,
+         np.zeros(3, np.int32)),                                                                  # open
+    ]
+    b = wl.batch_of(structs, tabs)
+    d3 = handle(tabs, precision)
+    pos, typ = to_dev(b)
+    out = d3.compute_batch(pos, typ, b.offsets, b.cells, b.pbc)
+    d3.sync_status()
+    ref = oracle_mod.compute_batch(b, PRM)
+    (assert_fp64_ok if precision == "fp64" else assert_mixed_ok)(out, ref, b.offsets)
+    assert out["E"][0].item() == 0.0 and out["E"][3].item() == 0.0
+
+
+def test_open_atoms_outside_cell(torch_cuda, oracle_mod):
+    """Open boundaries with atoms far outside the given cell (clamped into edge bins)."""
+    tabs = wl.carbon_table()
+    g = np.random.Generator(np.random.PCG64(9))
+    pos = g.uniform(-30, 40, (40, 3))
+    b = wl.batch_of([(pos, np.zeros(40, np.int32), np.eye(3) * 5.0, np.zeros(3, np.int32))], tabs)
+    d3 = handle(tabs, "fp64")
+    p, t = to_dev(b)
+    out = d3.compute_batch(p, t, b.offsets, b.cells, b.pbc)
+    d3.sync_status()
+    assert_fp64_ok(out, oracle_mod.compute_batch(b, PRM), b.offsets)
+
+
+def test_status_codes(torch_cuda):
+    from paper_2310_05279_gb300 import D3Error, _lib
+    b = wl.bilayer_ab_64()
+    d3 = handle(b.tables)
+    pos, typ = to_dev(b)
+    bad = pos.clone()
+    bad[5, 1] = float("nan")
+    with pytest.raises(D3Error) as e:
+        d3.compute_batch(bad, typ, b.offsets, b.cells, b.pbc)
+        d3.sync_status()
+    assert e.value.status == _lib.D3_ERR_NONFINITE
+    badt = typ.clone()
+    badt[3] = 7
+    d3b = handle(b.tables)
+    with pytest.raises(D3Error) as e:
+        d3b.compute_batch(pos, badt, b.offsets, b.cells, b.pbc)
+        d3b.sync_status()
+    assert e.value.status == _lib.D3_ERR_TYPE
+    d3c = handle(b.tables)
+    with pytest.raises(D3Error) as e:
+        d3c.compute_batch(pos, typ, b.offsets, np.zeros((1, 9)), b.pbc)
+    assert e.value.status == _lib.D3_ERR_ARG
+    # the handle stays usable after reported errors
+    out = d3c.compute_batch(pos, typ, b.offsets, b.cells, b.pbc)
+    d3c.sync_status()
+    assert np.isfinite(out["E"].cpu().numpy()).all()
+
+
+def test_capacity_regrow(torch_cuda, oracle_mod):
+    """Lists sized for one configuration overflow when the atoms are compressed
+    under the same geometry: the overflow is reported, never written past the
+    buffers, and the next call regrows and is exact."""
+    from paper_2310_05279_gb300 import D3Error, _lib
+    tabs = wl.carbon_table()
+    g = np.random.Generator(np.random.PCG64(2))
+    cell = np.eye(3) * 30.0
+    loose = g.uniform(0, 30, (60, 3))
+    dense = 12.0 + g.uniform(0, 6, (60, 3))
+    b1 = wl.batch_of([(loose, np.zeros(60, np.int32), cell, np.ones(3, np.int32))], tabs)
+    b2 = wl.batch_of([(dense, np.zeros(60, np.int32), cell, np.ones(3, np.int32))], tabs)
+    d3 = handle(tabs, "fp64")
+    p1, t1 = to_dev(b1)
+    d3.compute_batch(p1, t1, b1.offsets, b1.cells, b1.pbc)
+    d3.sync_status()
+    p2, t2 = to_dev(b2)
+    with pytest.raises(D3Error) as e:
+        d3.compute_batch(p2, t2, b2.offsets, b2.cells, b2.pbc)
+        d3.sync_status()
+    assert e.value.status == _lib.D3_ERR_CAPACITY
+    out = d3.compute_batch(p2, t2, b2.offsets, b2.cells, b2.pbc)
+    d3.sync_status()
+    assert_fp64_ok(out, oracle_mod.compute_batch(b2, PRM), b2.offsets)
+
+
+def test_cuda_graph_capture(torch_cuda):
+    """After the first (sizing) call, a compute call allocates nothing and does
+    not synchronise, so it can be captured in a CUDA graph and replayed."""
+    torch = torch_cuda
+    b = wl.uneven_batch(seed=17, nstruct=20, n_range=(30, 800))
+    d3 = handle(b.tables)
+    pos, typ = to_dev(b)
+    ref = d3.compute_batch(pos, typ, b.offsets, b.cells, b.pbc)
+    d3.sync_status()
+    ref = {k: v.clone() for k, v in ref.items()}
+    out = {k: torch.empty_like(v) for k, v in ref.items()}
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        d3.compute_batch(pos, typ, b.offsets, b.cells, b.pbc, out=out)
+    torch.cuda.current_stream().wait_stream(s)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        d3.compute_batch(pos, typ, b.offsets, b.cells, b.pbc, out=out)
+    for _ in range(3):
+        for v in out.values():
+            v.fill_(float("nan"))
+        graph.replay()
+        torch.cuda.synchronize()
+        for k in ref:
+            assert torch.equal(out[k], ref[k]), k
+    d3.sync_status()

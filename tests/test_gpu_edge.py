@@ -1,6 +1,6 @@
 """Edge cases and error reporting through the C ABI: empty inputs, structures
 with no atoms, cells smaller than the cutoff, open and slab boundaries, invalid
-inputs reported as status codes (never faults), capacity regrowth, and CUDA
+inputs reported as status codes (never faults), list and image capacity regrowth, and CUDA
 graph capture of a compute call."""
 import numpy as np
 import pytest
@@ -101,7 +101,7 @@ def test_status_codes(torch_cuda):
     assert np.isfinite(out["E"].cpu().numpy()).all()
 
 
-def test_capacity_regrow(torch_cuda, oracle_mod):
+def test_list_capacity_regrow(torch_cuda, oracle_mod):
     """Lists sized for one configuration overflow when the atoms are compressed
     under the same geometry: the overflow is reported, never written past the
     buffers, and the next call regrows and is exact."""
@@ -113,6 +113,37 @@ def test_capacity_regrow(torch_cuda, oracle_mod):
     dense = 12.0 + g.uniform(0, 6, (60, 3))
     b1 = wl.batch_of([(loose, np.zeros(60, np.int32), cell, np.ones(3, np.int32))], tabs)
     b2 = wl.batch_of([(dense, np.zeros(60, np.int32), cell, np.ones(3, np.int32))], tabs)
+    d3 = handle(tabs, "fp64")
+    p1, t1 = to_dev(b1)
+    d3.compute_batch(p1, t1, b1.offsets, b1.cells, b1.pbc)
+    d3.sync_status()
+    p2, t2 = to_dev(b2)
+    with pytest.raises(D3Error) as e:
+        d3.compute_batch(p2, t2, b2.offsets, b2.cells, b2.pbc)
+        d3.sync_status()
+    assert e.value.status == _lib.D3_ERR_CAPACITY
+    out = d3.compute_batch(p2, t2, b2.offsets, b2.cells, b2.pbc)
+    d3.sync_status()
+    assert_fp64_ok(out, oracle_mod.compute_batch(b2, PRM), b2.offsets)
+
+
+def test_image_capacity_regrow(torch_cuda, oracle_mod):
+    """The image capacity is sized on the first call of a geometry.  A later
+    call with the same cell but atoms placed where each needs 26 periodic
+    images (a lattice in the middle of a 20 A cell, with two atoms near the
+    corners stretching the occupied range) overflows it: the overflow is
+    reported, nothing is written past the buffers, and the next call regrows
+    and is exact."""
+    from paper_2310_05279_gb300 import D3Error, _lib
+    tabs = wl.carbon_table()
+    g = np.random.Generator(np.random.PCG64(2))
+    cell = np.eye(3) * 20.0
+    loose = g.uniform(0, 20, (66, 3))
+    ax = np.array([8.5, 9.5, 10.5, 11.5])
+    lattice = np.stack(np.meshgrid(ax, ax, ax, indexing="ij"), -1).reshape(-1, 3)
+    dense = np.concatenate([lattice, [[0.4, 0.4, 0.4], [19.6, 19.6, 19.6]]])
+    b1 = wl.batch_of([(loose, np.zeros(66, np.int32), cell, np.ones(3, np.int32))], tabs)
+    b2 = wl.batch_of([(dense, np.zeros(66, np.int32), cell, np.ones(3, np.int32))], tabs)
     d3 = handle(tabs, "fp64")
     p1, t1 = to_dev(b1)
     d3.compute_batch(p1, t1, b1.offsets, b1.cells, b1.pbc)

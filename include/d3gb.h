@@ -58,7 +58,11 @@ enum { D3_FP64 = 0, D3_MIXED = 1 };
 /* Functional parameters of Eq. 2 (s6, s8, a1, a2), the constants of Eqs. 3-4
  * (k1 = 16, k2 = 4/3 scales the tabulated covalent radii, k3 = 4), and the two
  * cutoffs R_pot and R_cn of the paper (12 A and 6 A by default).  skin_A is
- * added to both list radii; 0 rebuilds exact lists every call.
+ * added to both list radii.  With skin_A = 0 every compute call rebuilds the
+ * lists.  With skin_A > 0 a compute call first checks on the device whether
+ * any atom moved more than skin_A/2 since the last build; only then does the
+ * build run, otherwise the lists (and the periodic images) are reused and only
+ * the positions are refreshed.  No host synchronisation is involved either way.
  * precision: D3_MIXED evaluates distances, damping, the C6 interpolation and
  * the coordination-number terms in FP32 with FP64 accumulation of energies,
  * virials and dE/dn; D3_FP64 evaluates everything in FP64. */
@@ -155,6 +159,12 @@ d3_status d3_backward(d3_handle *h, int32_t B, const int64_t *offsets, const dou
 /* Synchronise the handle's last stream and report the first recorded
  * device-side problem (then clear it). */
 d3_status d3_sync_status(d3_handle *h);
+
+/* Number of neighbour builds the handle has executed on the device, sizing
+ * passes included (with skin_A > 0 this shows how often the lists were
+ * rebuilt).  *builds is host memory.  Synchronises the handle's last stream.
+ * The paper has no counterpart; this is a diagnostic of the list reuse. */
+d3_status d3_build_count(d3_handle *h, int64_t *builds);
 
 /* Human-readable description of the last error on this handle ("" if none). */
 const char *d3_last_error(const d3_handle *h);

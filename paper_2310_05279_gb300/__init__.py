@@ -203,6 +203,12 @@ class D3:
     def sync_status(self):
         self._check(self.lib.d3_sync_status(self.h))
 
+    def build_count(self) -> int:
+        """Neighbour builds executed on the device so far (synchronises)."""
+        n = C.c_int64()
+        self._check(self.lib.d3_build_count(self.h, C.byref(n)))
+        return n.value
+
 
 def version() -> str:
     return _lib.load().d3_version().decode()

@@ -63,6 +63,7 @@ struct Plan {
     DevBuf mem;
     Work w{};
     int* bsum = nullptr;  // scan scratch
+    int* gate = nullptr;  // list-reuse gate (device int)
     double* bwd_scratch = nullptr;
     int64_t bwd_scratch_n = 0;
 };
@@ -86,6 +87,7 @@ struct d3_handle {
     float2* d_exptab = nullptr;  // 2^(j/64), j = 0..63, FP32 hi + lo
     double* d_rk = nullptr;
     int* d_status = nullptr;
+    unsigned long long* d_nbuild = nullptr;  // builds executed on the device
     cudaStream_t last_stream = nullptr;
     std::string err;
     Plan plan;
@@ -319,6 +321,9 @@ d3_status plan_alloc(d3_handle* h, Plan& P) {
     A(w.cnt_cn, int, Nr);
     A(w.maxcnt, int, 2 * B);
     A(w.work_ctr, int, 1);
+    A(w.gate, int, 1);
+    A(w.xref, double, 3 * Nr);
+    A(w.wshift, double, 3 * Nr);
     A(w.cn, double, Nr);
     A(w.W, char, Nr * h->RP * rs);
     A(w.dW, char, Nr * h->RP * rs);
@@ -344,6 +349,12 @@ d3_status plan_alloc(d3_handle* h, Plan& P) {
     const double rld = list_radius(h, h->prm.rc_disp_A), rln = list_radius(h, h->prm.rc_cn_A);
     w.rl_disp2 = (float)(rld * rld);
     w.rl_cn2 = (float)(rln * rln);
+    const double half_skin = 0.5 * std::max(0.0, h->prm.skin_A) / kBohrA;
+    w.skin_half2 = half_skin * half_skin;
+    w.nbuild = h->d_nbuild;
+    int* gate = w.gate;
+    w.gate = nullptr;  // the plan's own Work builds unconditionally; enqueue_build gates a copy
+    P.gate = gate;
     e = cudaMemcpy(dgeo, P.geo.data(), sizeof(StructGeo) * B, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(doff, P.offsets.data(), sizeof(int64_t) * (B + 1), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(h, e, "geometry upload");
@@ -365,17 +376,20 @@ std::vector<cudaEvent_t> take_events(d3_handle* h, int n) {
     return v;
 }
 
-d3_status enqueue_build(d3_handle* h, Plan& P, const double* pos, const int32_t* types, cudaStream_t st) {
-    Work& w = P.w;
-    cudaError_t e = cudaMemsetAsync(w.cnt_real, 0, sizeof(int) * (P.ncells + 1), st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(w.cnt_ghost, 0, sizeof(int) * (P.ncells + 1), st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(w.ghost_count, 0, sizeof(int), st);
-    if (e == cudaSuccess && P.B > 0) e = cudaMemsetAsync(w.maxcnt, 0, sizeof(int) * 2 * P.B, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(w.work_ctr, 0, sizeof(int), st);
-    // occupied-range minima start at a huge float, maxima at +0
-    if (e == cudaSuccess && P.B > 0) e = cudaMemsetAsync(w.frange, 0x7f, sizeof(int) * 3 * P.B, st);
-    if (e == cudaSuccess && P.B > 0) e = cudaMemsetAsync(w.frange + 3 * P.B, 0, sizeof(int) * 3 * P.B, st);
-    if (e != cudaSuccess) return cuda_fail(h, e, "memset");
+// Enqueue the neighbour build.  gated (list reuse, skin > 0): a displacement
+// check first decides on the device whether the build runs; the sorted
+// positions are rewritten either way.
+d3_status enqueue_build(d3_handle* h, Plan& P, const double* pos, const int32_t* types, cudaStream_t st,
+                        bool gated = false) {
+    Work w = P.w;
+    cudaError_t e = cudaSuccess;
+    if (gated) {
+        w.gate = P.gate;
+        e = cudaMemsetAsync(w.gate, 0, sizeof(int), st);
+        if (e == cudaSuccess) e = launch_check(w, pos, st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "displacement check");
+        if (P.Nr > 0) h->launches += 1;
+    }
     e = launch_build_impl(w, pos, types, h->d_rk, P.bsum, st);
     if (e != cudaSuccess) return cuda_fail(h, e, "neighbour build launch");
     if (P.Nr > 0) h->launches += kBuildLaunches;
@@ -470,7 +484,7 @@ d3_status forward(d3_handle* h, int32_t B, const int64_t* offsets, const double*
         ev = take_events(h, 7);
         if (ev.size() == 7) cudaEventRecord(ev[0], st);
     }
-    s = enqueue_build(h, P, pos, types, st);
+    s = enqueue_build(h, P, pos, types, st, h->prm.skin_A > 0);
     if (s != D3_OK) return s;
     const Consts c = make_consts(h);
     const bool mixed = h->prm.precision == D3_MIXED;
@@ -555,6 +569,7 @@ d3_status d3_create(const d3_params* params, const d3_tables* tables, d3_handle*
     if (e == cudaSuccess) e = m.alloc(&h->d_exptab, 64);
     if (e == cudaSuccess) e = m.alloc(&h->d_rk, T);
     if (e == cudaSuccess) e = m.alloc(&h->d_status, 1);
+    if (e == cudaSuccess) e = m.alloc(&h->d_nbuild, 1);
     if (e == cudaSuccess) e = cudaMemcpy(h->d_nref, h->nref.data(), T * sizeof(int), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(h->d_cnref, h->cnref.data(), T * R * sizeof(double), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(h->d_c6f, c6f.data(), c6f.size() * sizeof(float), cudaMemcpyHostToDevice);
@@ -578,6 +593,7 @@ d3_status d3_create(const d3_params* params, const d3_tables* tables, d3_handle*
     }
     if (e == cudaSuccess) e = cudaMemcpy(h->d_exptab, ex2.data(), ex2.size() * sizeof(float2), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(h->d_status, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(h->d_nbuild, 0, sizeof(unsigned long long));
     if (e != cudaSuccess) {
         h->tabmem.release();
         delete h;
@@ -743,6 +759,16 @@ d3_status d3_sync_status(d3_handle* h) {
 }
 
 const char* d3_last_error(const d3_handle* h) { return h ? h->err.c_str() : "NULL handle"; }
+
+d3_status d3_build_count(d3_handle* h, int64_t* builds) {
+    if (!h || !builds) return D3_ERR_ARG;
+    cudaError_t e = cudaStreamSynchronize(h->last_stream);
+    unsigned long long n = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&n, h->d_nbuild, sizeof(n), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(h, e, "build count");
+    *builds = (int64_t)n;
+    return D3_OK;
+}
 
 d3_status d3_profile_enable(d3_handle* h, int32_t on) {
     if (!h) return D3_ERR_ARG;

@@ -21,6 +21,9 @@ namespace d3gb {
 
 namespace {
 
+// A build kernel does nothing when list reuse is on and no atom has moved enough.
+__device__ __forceinline__ bool skip_build(const Work& w) { return w.gate && *w.gate == 0; }
+
 __device__ inline int cell_id(const StructGeo& G, const double f[3]) {
     int c[3];
 #pragma unroll
@@ -48,7 +51,7 @@ __device__ inline int warp_aggregated_inc(int* ctr) {
 // range per periodic axis (as float bits: the fractions are >= 0).
 __global__ void __launch_bounds__(256) k_wrap(Work w, const double* __restrict__ pos, const int32_t* __restrict__ types) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= w.Nr) return;
+    if (i >= w.Nr || skip_build(w)) return;
     const int s = struct_of(w.offsets, w.B, i);
     const StructGeo& G = w.geo[s];
     double xb[3];
@@ -75,7 +78,12 @@ __global__ void __launch_bounds__(256) k_wrap(Work w, const double* __restrict__
         w.fw[3 * i + k] = f[k];
     }
 #pragma unroll
-    for (int a = 0; a < 3; ++a) w.xw[3 * i + a] = f[0] * G.H[a] + f[1] * G.H[3 + a] + f[2] * G.H[6 + a];
+    for (int a = 0; a < 3; ++a) {
+        const double xw = f[0] * G.H[a] + f[1] * G.H[3 + a] + f[2] * G.H[6 + a];
+        w.xw[3 * i + a] = xw;
+        w.xref[3 * i + a] = xb[a];
+        w.wshift[3 * i + a] = xw - xb[a];
+    }
     const int cid = cell_id(G, f);
     w.cell_of[i] = cid;
     w.slot_of[i] = atomicAdd(&w.cnt_real[cid], 1);
@@ -99,6 +107,7 @@ __global__ void __launch_bounds__(256) k_wrap(Work w, const double* __restrict__
 // radius / plane spacing) of the structure's occupied range.  Slots are
 // reserved once per block (each thread counts, the block scans, one atomic).
 __global__ void __launch_bounds__(256) k_images(Work w) {
+    if (skip_build(w)) return;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool live = i < w.Nr;
     const int s = live ? struct_of(w.offsets, w.B, i) : 0;
@@ -209,7 +218,8 @@ __device__ inline int block_exclusive_scan(int v, int* total) {
 }
 
 __global__ void k_scan_blocks(const int* __restrict__ cnt, int* __restrict__ start, int* __restrict__ bsum,
-                              int64_t n) {
+                              int64_t n, const int* gate) {
+    if (gate && *gate == 0) return;
     int64_t i = (int64_t)blockIdx.x * kScanBlock + threadIdx.x;
     int v = i < n ? cnt[i] : 0;
     int tot;
@@ -218,7 +228,8 @@ __global__ void k_scan_blocks(const int* __restrict__ cnt, int* __restrict__ sta
     if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
 }
 
-__global__ void k_scan_sums(int* bsum, int nb, int* start, int64_t n) {
+__global__ void k_scan_sums(int* bsum, int nb, int* start, int64_t n, const int* gate) {
+    if (gate && *gate == 0) return;
     int carry = 0;
     for (int base = 0; base < nb; base += kScanBlock) {
         int i = base + threadIdx.x;
@@ -232,7 +243,8 @@ __global__ void k_scan_sums(int* bsum, int nb, int* start, int64_t n) {
     if (threadIdx.x == 0) start[n] = carry;
 }
 
-__global__ void k_scan_add(int* start, const int* __restrict__ bsum, int64_t n) {
+__global__ void k_scan_add(int* start, const int* __restrict__ bsum, int64_t n, const int* gate) {
+    if (gate && *gate == 0) return;
     int64_t i = (int64_t)blockIdx.x * kScanBlock + threadIdx.x;
     if (i < n) start[i] += bsum[blockIdx.x];
 }
@@ -240,11 +252,12 @@ __global__ void k_scan_add(int* start, const int* __restrict__ bsum, int64_t n) 
 // ---- scatter into cell order
 __global__ void k_scatter_real(Work w) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= w.Nr) return;
+    if (i >= w.Nr || skip_build(w)) return;
     w.sorted_src[w.start_real[w.cell_of[i]] + w.slot_of[i]] = (int)i;
 }
 
 __global__ void k_scatter_ghost(Work w) {
+    if (skip_build(w)) return;
     int g = blockIdx.x * blockDim.x + threadIdx.x;
     int ng = min(*w.ghost_count, w.ghost_cap);
     if (g >= ng) return;
@@ -255,7 +268,7 @@ __global__ void k_scatter_ghost(Work w) {
 // (source, translation).
 __global__ void k_sort_cells(Work w) {
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= w.ncells) return;
+    if (c >= w.ncells || skip_build(w)) return;
     {
         int b = w.start_real[c], e = w.start_real[c + 1];
         for (int k = b + 1; k < e; ++k) {
@@ -284,6 +297,46 @@ __global__ void k_sort_cells(Work w) {
             w.gsorted[m + 1] = g;
         }
     }
+}
+
+// Zero the counters of a build (and count the build).
+__global__ void k_reset(Work w) {
+    if (skip_build(w)) return;
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k <= w.ncells) {
+        w.cnt_real[k] = 0;
+        w.cnt_ghost[k] = 0;
+    }
+    if (k < 2 * (int64_t)w.B) w.maxcnt[k] = 0;
+    // occupied-range minima start at a huge float, maxima at +0
+    if (k < 3 * (int64_t)w.B) {
+        w.frange[k] = 0x7f7f7f7f;
+        w.frange[3 * w.B + k] = 0;
+    }
+    if (k == 0) {
+        *w.ghost_count = 0;
+        *w.work_ctr = 0;
+        atomicAdd(w.nbuild, 1ull);
+    }
+}
+
+// List reuse: gate the build on the largest displacement since the last
+// build, and carry every atom's wrapped position along with its displacement
+// (the wrap overwrites it when the build runs).
+__global__ void __launch_bounds__(256) k_check(Work w, const double* __restrict__ pos) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= w.Nr) return;
+    double d2 = 0.0;
+    bool fin = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const double x = pos[3 * i + a] * (1.0 / kBohrA);
+        fin = fin && isfinite(x);
+        const double d = x - w.xref[3 * i + a];
+        d2 += d * d;
+        w.xw[3 * i + a] = x + w.wshift[3 * i + a];
+    }
+    if (!fin || !(d2 <= w.skin_half2)) atomicOr(w.gate, 1);
 }
 
 // Split position: hi on a 2^-10 bohr grid (exact in FP32 for |x| < 2^13 bohr),
@@ -425,6 +478,7 @@ __device__ __forceinline__ int64_t next_chunk(const Work& w, int lane) {
 // contiguous index ranges, four candidates loaded per step.  Appends are
 // staged in shared memory, 8 per list, and leave as whole 32-byte sectors.
 __global__ void __launch_bounds__(128) k_build_lists(Work w) {
+    if (skip_build(w)) return;
     const int lane = threadIdx.x & 31;
     const float rd2 = w.rl_disp2, rn2 = w.rl_cn2;
     const float4* __restrict__ H = w.hi;
@@ -471,28 +525,31 @@ __global__ void __launch_bounds__(128) k_build_lists(Work w) {
 
 inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
-cudaError_t scan(const int* cnt, int* start, int* bsum, int64_t n, cudaStream_t st) {
+cudaError_t scan(const int* cnt, int* start, int* bsum, int64_t n, const int* gate, cudaStream_t st) {
     const int nb = (int)nblk(n, kScanBlock);
-    k_scan_blocks<<<nb, kScanBlock, 0, st>>>(cnt, start, bsum, n);
-    k_scan_sums<<<1, kScanBlock, 0, st>>>(bsum, nb, start, n);
-    k_scan_add<<<nb, kScanBlock, 0, st>>>(start, bsum, n);
+    k_scan_blocks<<<nb, kScanBlock, 0, st>>>(cnt, start, bsum, n, gate);
+    k_scan_sums<<<1, kScanBlock, 0, st>>>(bsum, nb, start, n, gate);
+    k_scan_add<<<nb, kScanBlock, 0, st>>>(start, bsum, n, gate);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-// The cell-list build: binning, images, sort, fill, lists.  The caller has
-// zeroed cnt_real, cnt_ghost, ghost_count and maxcnt on the same stream.
+// The cell-list build: counters, binning, images, sort, fill, lists.  With
+// w.gate set, every step but the fill runs only when *w.gate != 0 (list
+// reuse); the fill always rewrites the sorted positions from w.xw.
 // bsum must hold nblk(ncells, 1024) ints; rk_tab holds k2*Rcov per type (bohr).
 cudaError_t launch_build_impl(const Work& w, const double* pos, const int32_t* types, const double* rk_tab,
                               int* bsum, cudaStream_t st) {
     if (w.Nr == 0) return cudaGetLastError();
     const int TB = 256;
+    const int64_t nreset = std::max<int64_t>(w.ncells + 1, 3 * (int64_t)w.B);
+    k_reset<<<nblk(nreset, TB), TB, 0, st>>>(w);
     k_wrap<<<nblk(w.Nr, TB), TB, 0, st>>>(w, pos, types);
     k_images<<<nblk(w.Nr, TB), TB, 0, st>>>(w);
-    cudaError_t e = scan(w.cnt_real, w.start_real, bsum, w.ncells, st);
+    cudaError_t e = scan(w.cnt_real, w.start_real, bsum, w.ncells, w.gate, st);
     if (e != cudaSuccess) return e;
-    e = scan(w.cnt_ghost, w.start_ghost, bsum, w.ncells, st);
+    e = scan(w.cnt_ghost, w.start_ghost, bsum, w.ncells, w.gate, st);
     if (e != cudaSuccess) return e;
     k_scatter_real<<<nblk(w.Nr, TB), TB, 0, st>>>(w);
     if (w.ghost_cap > 0) k_scatter_ghost<<<nblk(w.ghost_cap, TB), TB, 0, st>>>(w);
@@ -509,5 +566,11 @@ cudaError_t launch_build_impl(const Work& w, const double* pos, const int32_t* t
 }
 
 int64_t scan_scratch_ints(int64_t ncells) { return nblk(ncells, kScanBlock) + 1; }
+
+cudaError_t launch_check(const Work& w, const double* pos, cudaStream_t st) {
+    if (w.Nr == 0) return cudaGetLastError();
+    k_check<<<nblk(w.Nr, 256), 256, 0, st>>>(w, pos);
+    return cudaGetLastError();
+}
 
 }  // namespace d3gb

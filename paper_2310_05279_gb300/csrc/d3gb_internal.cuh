@@ -101,6 +101,12 @@ struct Work {
     int* cnt_cn;             // [Nr]
     int* maxcnt;             // [2*B] max list length per structure (disp, cn)
     int* work_ctr;           // [1] persistent-kernel work counter (zeroed before each build)
+    // list reuse (skin > 0): the build kernels run only while *gate != 0
+    int* gate;               // nullptr: unconditional build; else set by k_check when an atom moved > skin/2
+    double* xref;            // [Nr*3] positions (bohr, input order) at the last build
+    double* wshift;          // [Nr*3] translation the wrap applied at the last build (bohr)
+    double skin_half2;       // (skin / 2)^2, bohr^2
+    unsigned long long* nbuild;  // [1] builds executed
     int num_sms;
     float rl_disp2, rl_cn2;  // list radii squared, bohr^2
     // passes
@@ -186,6 +192,10 @@ __device__ inline int struct_of(const int64_t* off, int B, int64_t i) {
 // Launchers implemented in the build and pass translation units.
 namespace d3gb {
 cudaError_t launch_build(const Work& w, const double* pos, const int32_t* types, cudaStream_t st);
+// Displacement check of list reuse: sets *w.gate when an atom moved more than
+// skin/2 since the last build (or is not finite) and moves every atom's
+// wrapped position by its new displacement.
+cudaError_t launch_check(const Work& w, const double* pos, cudaStream_t st);
 // Device tables of one handle.
 struct Tabs {
     const void* c6;        // [T][T][R][R] real (float or double by precision)
@@ -201,5 +211,5 @@ struct Tabs {
 cudaError_t launch_forward(const Work& w, const Consts& c, bool mixed, const Tabs& tabs, double* E, double* F,
                            double* W, double* e_atom, double* cn_out, int B, cudaStream_t st, cudaEvent_t* marks);
 constexpr int kForwardLaunches = 6;  // kernels per forward pass (B > 0, N > 0)
-constexpr int kBuildLaunches = 13;   // kernels per neighbour build (N > 0, with images)
+constexpr int kBuildLaunches = 14;   // kernels per neighbour build (N > 0, with images)
 }  // namespace d3gb

@@ -136,6 +136,25 @@ d3_status d3_compute_batch_ex(d3_handle *h, int32_t B, const int64_t *offsets, c
                               const int32_t *types, const double *cells, const int32_t *pbc, double *E,
                               double *F, double *W, double *e_atom, double *cn, void *stream);
 
+/* As d3_compute_batch_ex, plus the per-atom virial of Eq. 7 (Sec. II A):
+ * w_atom device double[N][9], eV, input order, row-major 3x3 per atom,
+ *     W_i[a][b] = sum_{j != i} (r_ij)_a (dU_j/dr_ji)_b,   r_ij = x_j - x_i,
+ * with each site energy U_j of Eq. 2 written as a function of the vectors
+ * from atom j.  Through the coordination numbers U_j depends on r_ji directly
+ * (n_j), through n_i, and through the CNs of j's other partners; all three
+ * are included, so W_i is in general not symmetric, and sum_i W_i equals W.
+ * Requires w_atom != NULL when N > 0 (e_atom and cn may be NULL). */
+d3_status d3_compute_batch_atoms(d3_handle *h, int32_t B, const int64_t *offsets, const double *pos,
+                                 const int32_t *types, const double *cells, const int32_t *pbc, double *E,
+                                 double *F, double *W, double *e_atom, double *cn, double *w_atom,
+                                 void *stream);
+
+/* Per-atom heat current of Eq. 8, J_i = W_i . v_i, for n atoms (no handle):
+ * w_atom device double[n][9] as written by d3_compute_batch_atoms, vel device
+ * double[n][3] (any velocity unit), J device double[n][3] (eV times that unit).
+ * Enqueued on stream; D3_ERR_ARG on a negative n or NULL arrays. */
+d3_status d3_heat_current(int64_t n, const double *w_atom, const double *vel, double *J, void *stream);
+
 /* As d3_compute_batch with every array in HOST memory (page-locked memory
  * gives full copy speed): copies inputs to the device, computes, copies E, F,
  * W back and synchronises the stream before returning. */

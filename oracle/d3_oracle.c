@@ -72,6 +72,7 @@ typedef struct {
     int64_t i, j;
     double d[3]; /* x_j + T - x_i, bohr */
     double r;
+    int T[3];    /* lattice translation of j, in lattice vectors */
 } instance;
 
 /* ------------------------------------------------------------------ helpers */
@@ -164,6 +165,7 @@ static instance *find_instances(int64_t n, const double *x, const double *Hb, co
                             q->i = i; q->j = j;
                             q->d[0] = d[0]; q->d[1] = d[1]; q->d[2] = d[2];
                             q->r = sqrt(d2);
+                            q->T[0] = n0; q->T[1] = n1; q->T[2] = n2;
                         }
                     }
         rows[i] = row;
@@ -329,6 +331,141 @@ int d3_oracle_compute(const oracle_params *p, const oracle_tables *t, int64_t n,
         for (int k = 0; k < 4; ++k) dEdp[k] = dp[k] * eV;
 
     free(x); free(I); free(nc); free(Wt); free(dWt); free(eat); free(dEdn); free(Fb);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ per-atom virial (Eq. 7) */
+
+/*
+ * d3_oracle_atom_virial: the per-atom virial of Eq. 7,
+ *     W_i = sum_{j != i} r_ij (x) dU_j/dr_ji,   r_ij = x_j - x_i,
+ * for every atom of one structure, with the site energy U_j of Eq. 2 written as
+ * a function of the vectors from atom j (the representation the general
+ * many-body formulation behind Eqs. 5-7 uses).  U_j depends on r_ji
+ *   (1) directly, through its pair term with i (r < R_pot);
+ *   (2) through n_j, whose term f(r_ji) is in Eq. 4 (r < R_cn);
+ *   (3a) through n_i when i is a dispersion partner of j: every term of n_i is
+ *        f(|r_jc - r_ji|), so dn_i/dr_ji = -sum_c f'(r_ic) r_ic/r_ic;
+ *   (3b) through n_b of every other dispersion partner b of j that has i as a
+ *        CN neighbour: the term f(|r_ji - r_jb|) of n_b.
+ * Each term is taken per ordered instance (periodic images included) and
+ * added to W of the instance's real atom.  w_atom [n][9] in eV, row-major
+ * (row = component of r_ij, column = component of dU_j/dr_ji).
+ */
+int d3_oracle_atom_virial(const oracle_params *p, const oracle_tables *t, int64_t n, const double *pos,
+                          const int32_t *types, const double *cell, const int32_t *pbc, double *w_atom) {
+    if (n < 0 || !p || !t || !w_atom) return -1;
+    for (int64_t i = 0; i < n; ++i)
+        if (types[i] < 0 || types[i] >= t->ntypes) return -2;
+    const int R = t->max_ref;
+    const double rcd = p->rc_disp_A / ORACLE_BOHR_A, rcn = p->rc_cn_A / ORACLE_BOHR_A;
+    const double rmax = rcd > rcn ? rcd : rcn;
+    double Hb[9], Hi[9];
+    for (int k = 0; k < 9; ++k) Hb[k] = cell[k] / ORACLE_BOHR_A;
+    if (fabs(det3(Hb)) < 1e-12) return -3;
+    inv3(Hb, Hi);
+    const size_t nn = (size_t)(n > 0 ? n : 1);
+    double *x = (double *)malloc(3 * nn * sizeof(double));
+    for (int64_t i = 0; i < n; ++i) {
+        double xb[3] = {pos[3 * i] / ORACLE_BOHR_A, pos[3 * i + 1] / ORACLE_BOHR_A, pos[3 * i + 2] / ORACLE_BOHR_A};
+        double f[3];
+        for (int k = 0; k < 3; ++k) f[k] = xb[0] * Hi[k] + xb[1] * Hi[3 + k] + xb[2] * Hi[6 + k];
+        for (int k = 0; k < 3; ++k)
+            if (pbc[k]) {
+                f[k] -= floor(f[k]);
+                if (f[k] >= 1.0) f[k] -= 1.0;
+            }
+        for (int a = 0; a < 3; ++a) x[3 * i + a] = f[0] * Hb[a] + f[1] * Hb[3 + a] + f[2] * Hb[6 + a];
+    }
+    int m[3];
+    for (int k = 0; k < 3; ++k) m[k] = pbc[k] ? (int)ceil(rmax / plane_width(Hb, k)) : 0;
+    int64_t ni = 0;
+    instance *I = find_instances(n, x, Hb, m, rmax, &ni);
+    /* first instance of every atom's row */
+    int64_t *row = (int64_t *)calloc(nn + 1, sizeof(int64_t));
+    for (int64_t q = 0; q < ni; ++q) row[I[q].i + 1]++;
+    for (int64_t i = 0; i < n; ++i) row[i + 1] += row[i];
+
+    /* Eq. 4 and Eq. 3 */
+    double *nc = (double *)calloc(nn, sizeof(double));
+    for (int64_t q = 0; q < ni; ++q)
+        if (I[q].r < rcn) nc[I[q].i] += cn_term(I[q].r, p->k2 * (t->rcov[types[I[q].i]] + t->rcov[types[I[q].j]]), p->k1);
+    double *Wt = (double *)calloc((size_t)R * nn, sizeof(double));
+    double *dWt = (double *)calloc((size_t)R * nn, sizeof(double));
+    for (int64_t i = 0; i < n; ++i) ref_weights(t, types[i], nc[i], p->k3, Wt + R * i, dWt + R * i);
+
+    /* per dispersion instance (j -> b): dU_j/dr of the pair term and
+     * B = dU_j/dn_b; per atom: A_j = dU_j/dn_j */
+    double *Bq = (double *)calloc((size_t)(ni > 0 ? ni : 1), sizeof(double));
+    double *dUdr = (double *)calloc((size_t)(ni > 0 ? ni : 1), sizeof(double));
+    double *A = (double *)calloc(nn, sizeof(double));
+    for (int64_t q = 0; q < ni; ++q) {
+        const instance *s = &I[q];
+        if (!(s->r < rcd)) continue;
+        int tj = types[s->i], tb = types[s->j];
+        const double *cref = t->c6_ref + ((size_t)(tj * t->ntypes + tb) * R) * R;
+        double C6 = 0.0, dC6own = 0.0, dC6partner = 0.0;
+        for (int a = 0; a < R; ++a)
+            for (int b = 0; b < R; ++b) {
+                double c = cref[a * R + b];
+                C6 += Wt[R * s->i + a] * Wt[R * s->j + b] * c;
+                dC6own += dWt[R * s->i + a] * Wt[R * s->j + b] * c;
+                dC6partner += Wt[R * s->i + a] * dWt[R * s->j + b] * c;
+            }
+        double R0sq = 3.0 * t->sqrtq[tj] * t->sqrtq[tb];
+        double Rd = p->a1 * sqrt(R0sq) + p->a2_bohr;
+        double C8 = C6 * R0sq;
+        double r = s->r, r2 = r * r, r6 = r2 * r2 * r2, r8 = r6 * r2;
+        double d6 = r6 + pow(Rd, 6.0), d8 = r8 + pow(Rd, 8.0);
+        /* U_j contains -1/2 (s6 C6 / d6 + s8 C8 / d8) for this instance */
+        double dU_dC6 = -0.5 * (p->s6 / d6 + p->s8 * R0sq / d8);
+        A[s->i] += dU_dC6 * dC6own;
+        Bq[q] = dU_dC6 * dC6partner;
+        dUdr[q] = 0.5 * (p->s6 * C6 * 6.0 * r * r2 * r2 / (d6 * d6) + p->s8 * C8 * 8.0 * r6 * r / (d8 * d8));
+    }
+    /* G_i = sum over CN instances of i of f'(r) r_ic / r */
+    double *G = (double *)calloc(3 * nn, sizeof(double));
+    for (int64_t q = 0; q < ni; ++q) {
+        const instance *s = &I[q];
+        if (!(s->r < rcn)) continue;
+        double fp = cn_term_dr(s->r, p->k2 * (t->rcov[types[s->i]] + t->rcov[types[s->j]]), p->k1);
+        for (int a = 0; a < 3; ++a) G[3 * s->i + a] += fp * s->d[a] / s->r;
+    }
+    double *Wa = (double *)calloc(9 * nn, sizeof(double));
+    /* (1), (2), (3a): instance j -> i with vector d = r_ji; r_ij = -d */
+    for (int64_t q = 0; q < ni; ++q) {
+        const instance *s = &I[q];
+        int64_t j = s->i, i = s->j;
+        double g[3] = {0.0, 0.0, 0.0}; /* dU_j/dr_ji */
+        if (s->r < rcd)
+            for (int a = 0; a < 3; ++a) g[a] += dUdr[q] * s->d[a] / s->r - Bq[q] * G[3 * i + a];
+        if (s->r < rcn) {
+            double fp = cn_term_dr(s->r, p->k2 * (t->rcov[types[j]] + t->rcov[types[i]]), p->k1);
+            for (int a = 0; a < 3; ++a) g[a] += A[j] * fp * s->d[a] / s->r;
+        }
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) Wa[9 * i + 3 * a + b] += -s->d[a] * g[b];
+    }
+    /* (3b): j -> b (dispersion), b -> c (CN), c an instance other than j itself */
+    for (int64_t q1 = 0; q1 < ni; ++q1) {
+        const instance *s1 = &I[q1];
+        if (!(s1->r < rcd)) continue;
+        int64_t j = s1->i, b = s1->j;
+        for (int64_t q2 = row[b]; q2 < row[b + 1]; ++q2) {
+            const instance *s2 = &I[q2];
+            if (!(s2->r < rcn)) continue;
+            int64_t c = s2->j;
+            if (c == j && s1->T[0] + s2->T[0] == 0 && s1->T[1] + s2->T[1] == 0 && s1->T[2] + s2->T[2] == 0)
+                continue; /* the term of n_b from atom j itself depends on r_jb only: it is part of (3a) */
+            double fp = cn_term_dr(s2->r, p->k2 * (t->rcov[types[b]] + t->rcov[types[c]]), p->k1);
+            for (int a = 0; a < 3; ++a) {
+                double rij = -(s1->d[a] + s2->d[a]); /* vector from c's instance to j */
+                for (int bb = 0; bb < 3; ++bb) Wa[9 * c + 3 * a + bb] += rij * Bq[q1] * fp * s2->d[bb] / s2->r;
+            }
+        }
+    }
+    for (int64_t k = 0; k < 9 * n; ++k) w_atom[k] = Wa[k] * ORACLE_HARTREE_EV;
+    free(x); free(I); free(row); free(nc); free(Wt); free(dWt); free(Bq); free(dUdr); free(A); free(G); free(Wa);
     return 0;
 }
 

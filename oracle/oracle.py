@@ -4,7 +4,8 @@
 ``compute()`` evaluates one structure and ``compute_batch()`` loops over the
 structures of a batch in order.  Inputs are numpy arrays in Angstrom; outputs
 are E (eV), F (eV/A), W (eV, 3x3), the site energies U_i (eV), the
-coordination numbers n_i, dE/dn_i (eV) and dE/d(s6, s8, a1, a2) (eV).
+coordination numbers n_i, dE/dn_i (eV) and dE/d(s6, s8, a1, a2) (eV);
+``atom_virial()`` gives the per-atom virials of Eq. 7.
 """
 from __future__ import annotations
 
@@ -57,6 +58,9 @@ def _load():
         lib.d3_oracle_weights.restype = None
         lib.d3_oracle_weights.argtypes = [C.POINTER(_Tables), C.c_int, C.c_double, C.c_double, d, d]
         lib.d3_oracle_num_threads.restype = C.c_int
+        lib.d3_oracle_atom_virial.restype = C.c_int
+        lib.d3_oracle_atom_virial.argtypes = [C.POINTER(_Params), C.POINTER(_Tables), C.c_int64, d,
+                                              C.POINTER(C.c_int32), d, C.POINTER(C.c_int32), d]
         _lib = lib
     return _lib
 
@@ -113,6 +117,32 @@ def compute(pos, types, cell, pbc, tables, params: dict) -> dict:
     if rc != 0:
         raise ValueError(f"oracle rejected the input (code {rc})")
     return dict(E=float(E[0]), F=F, W=W.reshape(3, 3), e_atom=ea, cn=cn, dEdn=dEdn, dEdp=dEdp)
+
+
+def atom_virial(pos, types, cell, pbc, tables, params: dict) -> np.ndarray:
+    """Per-atom virial of Eq. 7 for one structure, [n, 3, 3] in eV
+    (W_i[a, b] = sum_j (r_ij)_a (dU_j/dr_ji)_b)."""
+    lib = _load()
+    p = params_from(params)
+    P = _Params(p["s6"], p["s8"], p["a1"], p["a2"], p["k1"], p["k2"], p["k3"], p["rc_disp"], p["rc_cn"])
+    th = _TableHold(tables)
+    pos = np.ascontiguousarray(pos, np.float64).reshape(-1, 3)
+    types = np.ascontiguousarray(types, np.int32).reshape(-1)
+    cell = np.ascontiguousarray(cell, np.float64).reshape(9)
+    pbc = np.ascontiguousarray(pbc, np.int32).reshape(3)
+    n = pos.shape[0]
+    Wa = np.zeros((n, 9))
+    rc = lib.d3_oracle_atom_virial(C.byref(P), C.byref(th.t), n, _ptr(pos, C.c_double), _ptr(types, C.c_int32),
+                                   _ptr(cell, C.c_double), _ptr(pbc, C.c_int32), _ptr(Wa, C.c_double))
+    if rc != 0:
+        raise ValueError(f"oracle rejected the input (code {rc})")
+    return Wa.reshape(n, 3, 3)
+
+
+def atom_virial_batch(batch, params: dict) -> np.ndarray:
+    """Eq. 7 per-atom virials of every structure of a batch, [N, 3, 3] in eV."""
+    out = [atom_virial(*batch.structure(s), batch.tables, params) for s in range(batch.nstruct)]
+    return np.concatenate(out) if out else np.zeros((0, 3, 3))
 
 
 def compute_batch(batch, params: dict, structures: Optional[list] = None) -> dict:

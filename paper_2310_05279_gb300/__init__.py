@@ -101,10 +101,11 @@ class D3:
         pbc = _host(pbc, np.int32).reshape(B, 3) if B > 0 else np.zeros((0, 3), np.int32)
         return B, offsets, cells, pbc
 
-    def compute_batch(self, pos, types, offsets, cells, pbc, e_atom: bool = False, cn: bool = False, out=None,
-                      stream=None) -> dict:
+    def compute_batch(self, pos, types, offsets, cells, pbc, e_atom: bool = False, cn: bool = False,
+                      w_atom: bool = False, out=None, stream=None) -> dict:
         """pos: cuda float64 (N,3) in A; types: cuda int32 (N,); offsets/cells/pbc: host arrays.
-        Returns cuda tensors E (B,) eV, F (N,3) eV/A, W (B,3,3) eV [, e_atom (N,), cn (N,)]."""
+        Returns cuda tensors E (B,) eV, F (N,3) eV/A, W (B,3,3) eV [, e_atom (N,), cn (N,),
+        w_atom (N,3,3) eV: the per-atom virial of Eq. 7]."""
         import torch
         B, offsets, cells, pbc = self._geom(offsets, cells, pbc)
         N = int(offsets[-1])
@@ -119,8 +120,20 @@ class D3:
                 out["e_atom"] = torch.empty(N, dtype=torch.float64, device=dev)
             if cn:
                 out["cn"] = torch.empty(N, dtype=torch.float64, device=dev)
+            if w_atom:
+                out["w_atom"] = torch.empty((N, 3, 3), dtype=torch.float64, device=dev)
         ea = out.get("e_atom")
         cnv = out.get("cn")
+        wa = out.get("w_atom")
+        if wa is not None:
+            st = self.lib.d3_compute_batch_atoms(self.h, B, offsets.ctypes.data_as(_lib._lp), _dptr(pos),
+                                                 _dptr(types), cells.ctypes.data_as(_lib._dp),
+                                                 pbc.ctypes.data_as(_lib._ip), _dptr(out["E"]), _dptr(out["F"]),
+                                                 _dptr(out["W"]), _dptr(ea) if ea is not None else None,
+                                                 _dptr(cnv) if cnv is not None else None, _dptr(wa),
+                                                 _stream_ptr(stream))
+            self._check(st)
+            return out
         st = self.lib.d3_compute_batch_ex(self.h, B, offsets.ctypes.data_as(_lib._lp), _dptr(pos), _dptr(types),
                                           cells.ctypes.data_as(_lib._dp), pbc.ctypes.data_as(_lib._ip),
                                           _dptr(out["E"]), _dptr(out["F"]), _dptr(out["W"]),
@@ -208,6 +221,20 @@ class D3:
         n = C.c_int64()
         self._check(self.lib.d3_build_count(self.h, C.byref(n)))
         return n.value
+
+
+def heat_current(w_atom, vel, stream=None):
+    """Per-atom heat current of Eq. 8, J_i = W_i . v_i (cuda float64 (N,3,3) and (N,3))."""
+    import torch
+    lib = _lib.load()
+    n = int(w_atom.shape[0])
+    assert w_atom.is_cuda and w_atom.dtype == torch.float64 and w_atom.is_contiguous() and w_atom.numel() == 9 * n
+    assert vel.is_cuda and vel.dtype == torch.float64 and vel.is_contiguous() and vel.numel() == 3 * n
+    J = torch.empty((n, 3), dtype=torch.float64, device=w_atom.device)
+    st = lib.d3_heat_current(n, _dptr(w_atom), _dptr(vel), _dptr(J), _stream_ptr(stream))
+    if st != _lib.D3_OK:
+        raise D3Error(st, "d3_heat_current failed")
+    return J
 
 
 def version() -> str:

@@ -39,6 +39,9 @@ SIGNATURES = {
     "d3_compute_batch": (C.c_int, [_vp, C.c_int32, _lp, _vp, _vp, _dp, _ip, _vp, _vp, _vp, _vp]),
     "d3_compute_batch_ex": (C.c_int, [_vp, C.c_int32, _lp, _vp, _vp, _dp, _ip, _vp, _vp, _vp, _vp, _vp, _vp]),
     "d3_compute_batch_host": (C.c_int, [_vp, C.c_int32, _lp, _vp, _vp, _dp, _ip, _vp, _vp, _vp, _vp]),
+    "d3_compute_batch_atoms": (C.c_int, [_vp, C.c_int32, _lp, _vp, _vp, _dp, _ip, _vp, _vp, _vp, _vp, _vp, _vp,
+                                         _vp]),
+    "d3_heat_current": (C.c_int, [C.c_int64, _vp, _vp, _vp, _vp]),
     "d3_backward": (C.c_int, [_vp, C.c_int32, _lp, _vp, _vp, _dp, _ip, _vp, _vp, _vp, _vp, _vp]),
     "d3_sync_status": (C.c_int, [_vp]),
     "d3_last_error": (C.c_char_p, [_vp]),

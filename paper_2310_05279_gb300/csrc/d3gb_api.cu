@@ -332,6 +332,7 @@ d3_status plan_alloc(d3_handle* h, Plan& P) {
     A(w.Fd, char, Nr * 4 * rs);
     A(w.eat, double, Nr);
     A(w.wv, double, 6 * Nr);
+    A(w.Pv, char, Nr * 4 * rs);
     int64_t maxn = 0;
     for (int s = 0; s < B; ++s) maxn = std::max<int64_t>(maxn, P.geo[s].natoms);
     w.max_natoms = maxn;
@@ -469,7 +470,7 @@ d3_status check_batch_args(d3_handle* h, int32_t B, const int64_t* offsets, cons
 
 d3_status forward(d3_handle* h, int32_t B, const int64_t* offsets, const double* pos, const int32_t* types,
                   const double* cells, const int32_t* pbc, double* E, double* F, double* W, double* e_atom,
-                  double* cn, cudaStream_t st) {
+                  double* cn, cudaStream_t st, double* w_atom = nullptr) {
     d3_status s = check_batch_args(h, B, offsets, pos, types, cells, pbc);
     if (s != D3_OK) return s;
     if (B > 0 && (!E || !W)) return fail(h, D3_ERR_ARG, "NULL E or W");
@@ -495,7 +496,7 @@ d3_status forward(d3_handle* h, int32_t B, const int64_t* offsets, const double*
     tb.nref = h->d_nref;
     tb.rcpair = h->d_rcpair;
     tb.exptab = h->d_exptab;
-    cudaError_t e = launch_forward(P.w, c, mixed, tb, E, F, W, e_atom, cn, B, st,
+    cudaError_t e = launch_forward(P.w, c, mixed, tb, E, F, W, e_atom, cn, w_atom, B, st,
                                    ev.size() == 7 ? ev.data() + 1 : nullptr);
     if (e != cudaSuccess) return cuda_fail(h, e, "forward launch");
     h->launches += (P.Nr > 0 ? kForwardLaunches - 1 : 1);
@@ -652,6 +653,18 @@ d3_status d3_compute_batch_ex(d3_handle* h, int32_t B, const int64_t* offsets, c
                               const int32_t* types, const double* cells, const int32_t* pbc, double* E, double* F,
                               double* W, double* e_atom, double* cn, void* stream) {
     return forward(h, B, offsets, pos, types, cells, pbc, E, F, W, e_atom, cn, (cudaStream_t)stream);
+}
+
+d3_status d3_compute_batch_atoms(d3_handle* h, int32_t B, const int64_t* offsets, const double* pos,
+                                 const int32_t* types, const double* cells, const int32_t* pbc, double* E,
+                                 double* F, double* W, double* e_atom, double* cn, double* w_atom, void* stream) {
+    if (h && B > 0 && offsets && offsets[B] > 0 && !w_atom) return fail(h, D3_ERR_ARG, "NULL w_atom");
+    return forward(h, B, offsets, pos, types, cells, pbc, E, F, W, e_atom, cn, (cudaStream_t)stream, w_atom);
+}
+
+d3_status d3_heat_current(int64_t n, const double* w_atom, const double* vel, double* J, void* stream) {
+    if (n < 0 || (n > 0 && (!w_atom || !vel || !J))) return D3_ERR_ARG;
+    return launch_heat(n, w_atom, vel, J, (cudaStream_t)stream) == cudaSuccess ? D3_OK : D3_ERR_CUDA;
 }
 
 d3_status d3_compute_batch(d3_handle* h, int32_t B, const int64_t* offsets, const double* pos,

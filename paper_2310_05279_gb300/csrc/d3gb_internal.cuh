@@ -118,6 +118,7 @@ struct Work {
     void* Fd;                // [Nr][4] real (direct forces)
     double* eat;             // [Nr] site energies, Ha
     double* wv;              // [Nr][6] per-atom virial (xx yy zz xy xz yz), Ha
+    void* Pv;                // [Nr][4] real: P_i = sum_j (dU_j/dn_i) r_ij (per-atom virial of Eq. 7 only)
     double* fin_part;        // [B][ceil(max_natoms / 4096)][7] chunk sums
     int64_t max_natoms;
     int* status;
@@ -208,8 +209,12 @@ struct Tabs {
 
 // marks (optional): 6 events recorded before the CN pass and after the CN,
 // weight, dispersion, chain and finalize passes.
+// w_atom (optional, device double[N][9]): per-atom virial of Eq. 7, eV.
 cudaError_t launch_forward(const Work& w, const Consts& c, bool mixed, const Tabs& tabs, double* E, double* F,
-                           double* W, double* e_atom, double* cn_out, int B, cudaStream_t st, cudaEvent_t* marks);
+                           double* W, double* e_atom, double* cn_out, double* w_atom, int B, cudaStream_t st,
+                           cudaEvent_t* marks);
+// Eq. 8 per atom: J_i = W_i . v_i (device arrays).
+cudaError_t launch_heat(int64_t n, const double* w_atom, const double* vel, double* J, cudaStream_t st);
 constexpr int kForwardLaunches = 6;  // kernels per forward pass (B > 0, N > 0)
 constexpr int kBuildLaunches = 14;   // kernels per neighbour build (N > 0, with images)
 }  // namespace d3gb

@@ -411,7 +411,9 @@ __global__ void __launch_bounds__(128) k_weights(Work w, Consts c, const double*
 
 // ------------------------------------------------------------------ Eq. 2
 // pair table per (t_i, t_j): x = R^6, y = R^8, z = s6, w = s8 R0^2 (bohr, R = a1 R0 + a2)
-template <bool MIXED, int R>
+// ATOMV: also form P_i = sum_j (dU_j/dn_i) r_ij for the per-atom virial of Eq. 7
+// (dU_j/dn_i = -1/2 (dE_ij/dC6) dC6_ij/dn_i for the pair term of U_j).
+template <bool MIXED, int R, bool ATOMV>
 __global__ void __launch_bounds__(128) k_disp(Work w, Consts c, const typename Real<MIXED>::T4* __restrict__ pair_tab) {
     using T = typename Real<MIXED>::T;
     using T4 = typename Real<MIXED>::T4;
@@ -436,9 +438,11 @@ __global__ void __launch_bounds__(128) k_disp(Work w, Consts c, const typename R
     T fx = 0, fy = 0, fz = 0;
     T dnh = 0, dnl = 0;  // dE/dn_i, compensated (it scales the chain-rule forces)
     double E = 0, Sxx = 0, Syy = 0, Szz = 0, Sxy = 0, Sxz = 0, Syz = 0;
+    double Px = 0, Py = 0, Pz = 0;
     for (int k0 = 0; k0 < cnt; k0 += kChunk) {
         const int k1e = min(cnt, k0 + kChunk);
         T e = 0, sxx = 0, syy = 0, szz = 0, sxy = 0, sxz = 0, syz = 0;
+        T px = 0, py = 0, pz = 0;
         LV.for_each(k0, k1e, [&](int q) {
             T dx, dy, dz, r2, rkq;
             int tsq;
@@ -461,6 +465,10 @@ __global__ void __launch_bounds__(128) k_disp(Work w, Consts c, const typename R
             const T g = t6 + t8;                     // -de/dC6
             e = fma(-C6, g, e);
             acc_add(dnh, dnl, -g * dC6);
+            if constexpr (ATOMV) {
+                const T b = (T)-0.5 * g * dC6;
+                px = fma(b, dx, px); py = fma(b, dy, py); pz = fma(b, dz, pz);
+            }
             // 2 de/d(r^2): F_i += (de/dr) d/r = fc d
             const T fc = C6 * fma((T)6 * r4, t6 * i6, (T)8 * r6 * (t8 * i8));
             const T tx = fc * dx, ty = fc * dy, tz = fc * dz;
@@ -471,7 +479,9 @@ __global__ void __launch_bounds__(128) k_disp(Work w, Consts c, const typename R
         E += (double)e;
         Sxx += (double)sxx; Syy += (double)syy; Szz += (double)szz;
         Sxy += (double)sxy; Sxz += (double)sxz; Syz += (double)syz;
+        Px += (double)px; Py += (double)py; Pz += (double)pz;
     }
+    if constexpr (ATOMV) ((T4*)w.Pv)[p] = T4{(T)Px, (T)Py, (T)Pz, (T)0};
     ((T*)w.dEdn)[p] = (T)((double)dnh + (double)dnl);
     ((T4*)w.Fd)[p] = T4{fx, fy, fz, (T)0};
     w.eat[p] = 0.5 * E;
@@ -487,10 +497,18 @@ __global__ void __launch_bounds__(128) k_disp(Work w, Consts c, const typename R
 // happens in FP64 (per-atom sums and the per-structure reduction).  The force
 // coefficient (dE/dn_i + dE/dn_q) f'(r)/r uses the double-single argument, the
 // exact rc and 1/r from the double-single r^2.
-template <bool MIXED>
+//
+// ATOMV: also the per-atom virial of Eq. 7 (row-major, eV) into w_atom:
+//   W_i = D_i - sum_j dE/dn_j f'(r)/r d (x) d - P_i (x) G_i - sum_j f'(r)/r P_j (x) d,
+// d = r_ij, G_i = sum_j f'(r)/r d, D_i the half-and-half direct pair virial of
+// the dispersion pass and P from it.  The first sum is the dependence of the
+// partners' site energies on r_ji through their own coordination numbers, the
+// last two the dependence through n_i and through the CNs of other partners.
+template <bool MIXED, bool ATOMV>
 __global__ void __launch_bounds__(128) k_chain(Work w, Consts c, const float4* __restrict__ rcpair,
                                               const float2* __restrict__ exptab, double* __restrict__ F,
-                                              double* __restrict__ e_atom, double* __restrict__ cn_out) {
+                                              double* __restrict__ e_atom, double* __restrict__ cn_out,
+                                              double* __restrict__ w_atom) {
     using T = typename Real<MIXED>::T;
     using T4 = typename Real<MIXED>::T4;
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -504,11 +522,14 @@ __global__ void __launch_bounds__(128) k_chain(Work w, Consts c, const float4* _
     const T rc2 = (T)c.rc_cn2, k1 = (T)c.k1;
     T fx = 0, fy = 0, fz = 0;
     double Sxx = 0, Syy = 0, Szz = 0, Sxy = 0, Sxz = 0, Syz = 0;
+    double Tm[6] = {0, 0, 0, 0, 0, 0}, Gv[3] = {0, 0, 0}, Mm[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     for (int k0 = 0; k0 < cnt; k0 += kChunk) {
         const int k1e = min(cnt, k0 + kChunk);
         T sxx = 0, syy = 0, szz = 0, sxy = 0, sxz = 0, syz = 0;
+        T tm[6] = {0, 0, 0, 0, 0, 0}, gv[3] = {0, 0, 0}, mm[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
         LV.for_each(k0, k1e, [&](int q) {
             T dx, dy, dz, g, dnq;
+            int srcq;
             if constexpr (MIXED) {
                 float D[3], r2, ah, al, rch, rcl, r2l;
                 int tq;
@@ -529,7 +550,8 @@ __global__ void __launch_bounds__(128) k_chain(Work w, Consts c, const float4* _
                 ds_mul(rch, rcl, cfh, cfl, uh, ul);
                 ds_mul(uh, ul, a3h, a3l, gh, gl);
                 g = -k1 * (gh + gl);
-                dnq = dEdn[tq >> 4];
+                srcq = tq >> 4;
+                dnq = dEdn[srcq];
                 dx = D[0]; dy = D[1]; dz = D[2];
             } else {
                 T r2, rkq;
@@ -540,7 +562,8 @@ __global__ void __launch_bounds__(128) k_chain(Work w, Consts c, const float4* _
                 T f, dfdr;
                 cn_fun(rinv, S.rk() + rkq, (T)0, k1, f, &dfdr);
                 g = dfdr * rinv;
-                dnq = dEdn[tsq >> 4];
+                srcq = tsq >> 4;
+                dnq = dEdn[srcq];
             }
             const T coef = (dni + dnq) * g;
             fx += coef * dx; fy += coef * dy; fz += coef * dz;
@@ -548,9 +571,28 @@ __global__ void __launch_bounds__(128) k_chain(Work w, Consts c, const float4* _
             const T gx = g * dx, gy = g * dy, gz = g * dz;
             sxx = fma(gx, dx, sxx); syy = fma(gy, dy, syy); szz = fma(gz, dz, szz);
             sxy = fma(gx, dy, sxy); sxz = fma(gx, dz, sxz); syz = fma(gy, dz, syz);
+            if constexpr (ATOMV) {
+                const T4 Pq = ((const T4*)w.Pv)[srcq];
+                const T hx = dnq * gx, hy = dnq * gy, hz = dnq * gz;
+                tm[0] = fma(hx, dx, tm[0]); tm[1] = fma(hy, dy, tm[1]); tm[2] = fma(hz, dz, tm[2]);
+                tm[3] = fma(hx, dy, tm[3]); tm[4] = fma(hx, dz, tm[4]); tm[5] = fma(hy, dz, tm[5]);
+                gv[0] += gx; gv[1] += gy; gv[2] += gz;
+                const T ga = g * Pq.x, gb = g * Pq.y, gc = g * Pq.z;
+                mm[0] = fma(ga, dx, mm[0]); mm[1] = fma(ga, dy, mm[1]); mm[2] = fma(ga, dz, mm[2]);
+                mm[3] = fma(gb, dx, mm[3]); mm[4] = fma(gb, dy, mm[4]); mm[5] = fma(gb, dz, mm[5]);
+                mm[6] = fma(gc, dx, mm[6]); mm[7] = fma(gc, dy, mm[7]); mm[8] = fma(gc, dz, mm[8]);
+            }
         });
         Sxx += (double)sxx; Syy += (double)syy; Szz += (double)szz;
         Sxy += (double)sxy; Sxz += (double)sxz; Syz += (double)syz;
+        if constexpr (ATOMV) {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) Tm[k] += (double)tm[k];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) Gv[k] += (double)gv[k];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) Mm[k] += (double)mm[k];
+        }
     }
     const T4 fd = ((const T4*)w.Fd)[p];
     const double u = kHartreeEV / kBohrA;
@@ -558,9 +600,22 @@ __global__ void __launch_bounds__(128) k_chain(Work w, Consts c, const float4* _
     F[3 * (int64_t)i + 0] = ((double)fd.x + (double)fx) * u;
     F[3 * (int64_t)i + 1] = ((double)fd.y + (double)fy) * u;
     F[3 * (int64_t)i + 2] = ((double)fd.z + (double)fz) * u;
+    double* wv = w.wv + 6 * p;
+    if constexpr (ATOMV) {
+        // wv holds the direct (dispersion) part here: xx yy zz xy xz yz
+        const double Dm[9] = {wv[0], wv[3], wv[4], wv[3], wv[1], wv[5], wv[4], wv[5], wv[2]};
+        const double Ts[9] = {Tm[0], Tm[3], Tm[4], Tm[3], Tm[1], Tm[5], Tm[4], Tm[5], Tm[2]};
+        const T4 Pi = ((const T4*)w.Pv)[p];
+        const double P[3] = {(double)Pi.x, (double)Pi.y, (double)Pi.z};
+        double* out = w_atom + 9 * (int64_t)i;
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b)
+                out[3 * a + b] = (Dm[3 * a + b] - Ts[3 * a + b] - P[a] * Gv[b] - Mm[3 * a + b]) * kHartreeEV;
+    }
     // W -= sum over ordered pairs of dE/dn_i f'(r) d(x)d/r
     const double dn = (double)dni;
-    double* wv = w.wv + 6 * p;
     wv[0] -= dn * Sxx; wv[1] -= dn * Syy; wv[2] -= dn * Szz;
     wv[3] -= dn * Sxy; wv[4] -= dn * Sxz; wv[5] -= dn * Syz;
     if (e_atom) e_atom[i] = w.eat[p] * kHartreeEV;
@@ -619,7 +674,8 @@ inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
 template <bool MIXED, int R>
 cudaError_t forward_impl(const Work& w, const Consts& c, const Tabs& tb, double* E, double* F, double* W,
-                         double* e_atom, double* cn_out, int B, cudaStream_t st, cudaEvent_t* marks) {
+                         double* e_atom, double* cn_out, double* w_atom, int B, cudaStream_t st,
+                         cudaEvent_t* marks) {
     using T = typename Real<MIXED>::T;
     using T4 = typename Real<MIXED>::T4;
     const int TB = 128;
@@ -631,9 +687,19 @@ cudaError_t forward_impl(const Work& w, const Consts& c, const Tabs& tb, double*
     mark(1);
     if (w.Nr > 0) k_weights<MIXED, R><<<nblk(w.Nr, TB), TB, 0, st>>>(w, c, tb.cnref, tb.nref, (const T*)tb.c6);
     mark(2);
-    if (w.Nr > 0) k_disp<MIXED, R><<<nblk(w.Nr, TB), TB, c.T * c.T * sizeof(T4), st>>>(w, c, (const T4*)tb.pair);
+    if (w.Nr > 0) {
+        if (w_atom)
+            k_disp<MIXED, R, true><<<nblk(w.Nr, TB), TB, c.T * c.T * sizeof(T4), st>>>(w, c, (const T4*)tb.pair);
+        else
+            k_disp<MIXED, R, false><<<nblk(w.Nr, TB), TB, c.T * c.T * sizeof(T4), st>>>(w, c, (const T4*)tb.pair);
+    }
     mark(3);
-    if (w.Nr > 0) k_chain<MIXED><<<nblk(w.Nr, TB), TB, 0, st>>>(w, c, tb.rcpair, tb.exptab, F, e_atom, cn_out);
+    if (w.Nr > 0) {
+        if (w_atom)
+            k_chain<MIXED, true><<<nblk(w.Nr, TB), TB, 0, st>>>(w, c, tb.rcpair, tb.exptab, F, e_atom, cn_out, w_atom);
+        else
+            k_chain<MIXED, false><<<nblk(w.Nr, TB), TB, 0, st>>>(w, c, tb.rcpair, tb.exptab, F, e_atom, cn_out, nullptr);
+    }
     mark(4);
     if (B > 0) {
         const int nchunk = (int)((w.max_natoms + kFinChunk - 1) / kFinChunk);
@@ -644,11 +710,28 @@ cudaError_t forward_impl(const Work& w, const Consts& c, const Tabs& tb, double*
     return cudaGetLastError();
 }
 
+// Eq. 8: J_i = W_i . v_i (row-major W_i)
+__global__ void k_heat(int64_t n, const double* __restrict__ w_atom, const double* __restrict__ vel,
+                       double* __restrict__ J) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double* Wi = w_atom + 9 * i;
+    const double v0 = vel[3 * i], v1 = vel[3 * i + 1], v2 = vel[3 * i + 2];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) J[3 * i + a] = Wi[3 * a] * v0 + Wi[3 * a + 1] * v1 + Wi[3 * a + 2] * v2;
+}
+
 }  // namespace
 
+cudaError_t launch_heat(int64_t n, const double* w_atom, const double* vel, double* J, cudaStream_t st) {
+    if (n > 0) k_heat<<<nblk(n, 256), 256, 0, st>>>(n, w_atom, vel, J);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_forward(const Work& w, const Consts& c, bool mixed, const Tabs& tabs, double* E, double* F,
-                           double* W, double* e_atom, double* cn_out, int B, cudaStream_t st, cudaEvent_t* marks) {
-#define D3_FWD(M, RR) return forward_impl<M, RR>(w, c, tabs, E, F, W, e_atom, cn_out, B, st, marks)
+                           double* W, double* e_atom, double* cn_out, double* w_atom, int B, cudaStream_t st,
+                           cudaEvent_t* marks) {
+#define D3_FWD(M, RR) return forward_impl<M, RR>(w, c, tabs, E, F, W, e_atom, cn_out, w_atom, B, st, marks)
     if (mixed) {
         switch (c.R) {
             case 1: D3_FWD(true, 1);

@@ -104,6 +104,13 @@ void d3_destroy(d3_handle *h);
  * Takes effect for work enqueued afterwards on the handle's last stream. */
 d3_status d3_set_damping(d3_handle *h, double s6, double s8, double a1, double a2_bohr);
 
+/* Accumulate mode for the NEP-D3 sum of Eq. 9 (U = U_NEP + U_D3, Sec. II A):
+ * with on != 0, the compute calls ADD their E, F and W into the caller's
+ * output arrays (which then hold, e.g., the short-range model's values)
+ * instead of overwriting them.  Site energies, CNs and per-atom virials are
+ * always overwritten.  Default off.  Applies to work enqueued afterwards. */
+d3_status d3_set_accumulate(d3_handle *h, int32_t on);
+
 /* Build (or rebuild) the neighbour lists of a batch and size the workspace
  * for it; synchronises.  The cell-list build: wrap into the cell, periodic
  * image atoms within the list radius, counting sort by cell, and per-atom

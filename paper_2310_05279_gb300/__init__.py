@@ -216,6 +216,10 @@ class D3:
     def sync_status(self):
         self._check(self.lib.d3_sync_status(self.h))
 
+    def set_accumulate(self, on: bool = True):
+        """Add E, F, W into the output tensors instead of overwriting them (Eq. 9 coupling)."""
+        self._check(self.lib.d3_set_accumulate(self.h, 1 if on else 0))
+
     def build_count(self) -> int:
         """Neighbour builds executed on the device so far (synchronises)."""
         n = C.c_int64()

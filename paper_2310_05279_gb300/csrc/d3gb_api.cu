@@ -103,6 +103,7 @@ struct d3_handle {
     double prof_ms[6] = {0, 0, 0, 0, 0, 0};
     int64_t prof_calls[6] = {0, 0, 0, 0, 0, 0};
     int64_t launches = 0;
+    bool accumulate = false;  // d3_set_accumulate
 };
 
 namespace {
@@ -169,6 +170,7 @@ Consts make_consts(const d3_handle* h) {
     c.T = h->T;
     c.R = h->R;
     c.RP = h->RP;
+    c.accumulate = h->accumulate ? 1 : 0;
     return c;
 }
 
@@ -631,6 +633,12 @@ d3_status d3_set_damping(d3_handle* h, double s6, double s8, double a1, double a
     h->prm.a1 = a1;
     h->prm.a2_bohr = a2_bohr;
     return upload_pair_table(h);
+}
+
+d3_status d3_set_accumulate(d3_handle* h, int32_t on) {
+    if (!h) return D3_ERR_ARG;
+    h->accumulate = on != 0;
+    return D3_OK;
 }
 
 d3_status d3_build_neighbors(d3_handle* h, int32_t B, const int64_t* offsets, const double* pos,

@@ -130,6 +130,7 @@ struct Consts {
     double k1, k3;
     double s6, s8, a1, a2;     // damping of Eq. 2 (a2 in bohr)
     int T, R, RP;
+    int accumulate;            // add E, F, W into the outputs instead of overwriting them
 };
 
 // ---- neighbour lists: one row of `cap` entries per atom (cap a multiple of 8),

@@ -597,9 +597,14 @@ __global__ void __launch_bounds__(128) k_chain(Work w, Consts c, const float4* _
     const T4 fd = ((const T4*)w.Fd)[p];
     const double u = kHartreeEV / kBohrA;
     const int i = w.perm[p];
-    F[3 * (int64_t)i + 0] = ((double)fd.x + (double)fx) * u;
-    F[3 * (int64_t)i + 1] = ((double)fd.y + (double)fy) * u;
-    F[3 * (int64_t)i + 2] = ((double)fd.z + (double)fz) * u;
+    const double f0 = ((double)fd.x + (double)fx) * u, f1 = ((double)fd.y + (double)fy) * u,
+                 f2 = ((double)fd.z + (double)fz) * u;
+    double* Fi = F + 3 * (int64_t)i;
+    if (c.accumulate) {
+        Fi[0] += f0; Fi[1] += f1; Fi[2] += f2;
+    } else {
+        Fi[0] = f0; Fi[1] = f1; Fi[2] = f2;
+    }
     double* wv = w.wv + 6 * p;
     if constexpr (ATOMV) {
         // wv holds the direct (dispersion) part here: xx yy zz xy xz yz
@@ -653,7 +658,7 @@ __global__ void __launch_bounds__(256) k_fin_chunks(Work w, double* __restrict__
 }
 
 __global__ void k_fin_struct(Work w, const double* __restrict__ part, int nchunk, double* __restrict__ E,
-                             double* __restrict__ Wout) {
+                             double* __restrict__ Wout, int accumulate) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= w.B) return;
     const int nc = (w.geo[s].natoms + kFinChunk - 1) / kFinChunk;
@@ -662,12 +667,18 @@ __global__ void k_fin_struct(Work w, const double* __restrict__ part, int nchunk
 #pragma unroll
         for (int m = 0; m < 7; ++m) acc[m] += part[((int64_t)s * nchunk + ch) * 7 + m];
     const double h = kHartreeEV;
-    E[s] = acc[0] * h;
+    const double v[9] = {acc[1] * h, acc[4] * h, acc[5] * h, acc[4] * h, acc[2] * h, acc[6] * h,
+                         acc[5] * h, acc[6] * h, acc[3] * h};
     double* Ws = Wout + 9 * (int64_t)s;
-    Ws[0] = acc[1] * h; Ws[4] = acc[2] * h; Ws[8] = acc[3] * h;
-    Ws[1] = Ws[3] = acc[4] * h;
-    Ws[2] = Ws[6] = acc[5] * h;
-    Ws[5] = Ws[7] = acc[6] * h;
+    if (accumulate) {
+        E[s] += acc[0] * h;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) Ws[k] += v[k];
+    } else {
+        E[s] = acc[0] * h;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) Ws[k] = v[k];
+    }
 }
 
 inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
@@ -704,7 +715,7 @@ cudaError_t forward_impl(const Work& w, const Consts& c, const Tabs& tb, double*
     if (B > 0) {
         const int nchunk = (int)((w.max_natoms + kFinChunk - 1) / kFinChunk);
         if (nchunk > 0) k_fin_chunks<<<dim3(B, nchunk), 256, 0, st>>>(w, w.fin_part, nchunk);
-        k_fin_struct<<<nblk(B, 128), 128, 0, st>>>(w, w.fin_part, nchunk > 0 ? nchunk : 1, E, W);
+        k_fin_struct<<<nblk(B, 128), 128, 0, st>>>(w, w.fin_part, nchunk > 0 ? nchunk : 1, E, W, c.accumulate);
     }
     mark(5);
     return cudaGetLastError();

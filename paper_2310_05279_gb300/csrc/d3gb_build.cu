@@ -35,18 +35,6 @@ __device__ inline int cell_id(const StructGeo& G, const double f[3]) {
     return (int)(G.cell_base + ((int64_t)c[2] * G.ncell[1] + c[1]) * G.ncell[0] + c[0]);
 }
 
-// Slot in a shared counter for every active lane of the warp, one atomic per warp.
-__device__ inline int warp_aggregated_inc(int* ctr) {
-    unsigned mask = __activemask();
-    int lane = threadIdx.x & 31;
-    int leader = __ffs(mask) - 1;
-    int rank = __popc(mask & ((1u << lane) - 1u));
-    int base = 0;
-    if (lane == leader) base = atomicAdd(ctr, __popc(mask));
-    base = __shfl_sync(mask, base, leader);
-    return base + rank;
-}
-
 // Wrap into the cell, bin, and record each structure's occupied fractional
 // range per periodic axis (as float bits: the fractions are >= 0).
 __global__ void __launch_bounds__(256) k_wrap(Work w, const double* __restrict__ pos, const int32_t* __restrict__ types) {

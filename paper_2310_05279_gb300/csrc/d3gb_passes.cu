@@ -28,11 +28,6 @@ __device__ __forceinline__ float rcp_approx(float x) {
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
 }
-__device__ __forceinline__ float ex2_approx(float x) {
-    float r;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
 __device__ __forceinline__ float rsqrt_approx(float x) {
     float r;
     asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
@@ -131,19 +126,13 @@ template <> struct Site<false> {
     __device__ bool inside(int, double r2, double rc2, double) const { return r2 < rc2; }
 };
 
-// Eq. 4 counting function f(r) and, optionally, df/dr; r from 1/r.
-__device__ __forceinline__ void cn_fun(float rinv, float rc_eff, float k1l2e, float k1, float& f, float* dfdr) {
-    // exp(-k1 (rc_eff/r - 1)) = 2^(k1 log2(e) (1 - rc_eff/r))
-    const float t = ex2_approx(k1l2e * fmaf(-rc_eff, rinv, 1.0f));
-    f = rcp_nr(1.0f + t);
-    if (dfdr) *dfdr = -k1 * rc_eff * rinv * rinv * t * f * f;
-}
+// Eq. 4 counting function f(r) and, optionally, df/dr, in FP64; r from 1/r.
+// (The mixed form evaluates it in double-single, cn_ds below.)
 __device__ __forceinline__ void cn_fun(double rinv, double rc_eff, double, double k1, double& f, double* dfdr) {
     const double t = exp(-k1 * (rc_eff * rinv - 1.0));
     f = 1.0 / (1.0 + t);
     if (dfdr) *dfdr = -k1 * rc_eff * rinv * rinv * t * f * f;
 }
-__device__ __forceinline__ float inv_sqrt(float x) { return rsqrt_nr(x); }
 __device__ __forceinline__ double inv_sqrt(double x) { return 1.0 / sqrt(x); }
 __device__ __forceinline__ float recip(float x) { return rcp_approx(x); }
 __device__ __forceinline__ double recip(double x) { return 1.0 / x; }

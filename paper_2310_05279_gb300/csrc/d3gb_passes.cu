@@ -4,9 +4,10 @@
 // so no pass needs atomics and every sum has a fixed order.
 //
 //   k_cn       Eq. 4  n_i = sum_j 1/(1 + exp(-k1 (k2 (Rcov_i + Rcov_j)/r - 1)))
-//   k_weights  Eq. 3  per-atom normalised Gaussian weights W_ia, dW_ia/dn_i and
-//                     the projections v_i^(t)_a = sum_b C6ref[t][t_i][a][b] W_ib,
-//                     so that C6_ij = sum_a W_ia v_j^(t_i)_a
+//              and Eq. 3 per atom at the end of the same thread: normalised
+//                     Gaussian weights W_ia, dW_ia/dn_i and the projections
+//                     v_i^(t)_a = sum_b C6ref[t][t_i][a][b] W_ib, so that
+//                     C6_ij = sum_a W_ia v_j^(t_i)_a
 //   k_disp     Eq. 2  site energy, direct forces, virial and
 //                     dE/dn_i = sum_j (dE/dC6_ij)(dC6_ij/dn_i)
 //   k_chain           forces and virial of the coordination-number dependence:
@@ -279,15 +280,100 @@ __device__ __forceinline__ void ds_mul(float ah, float al, float bh, float bl, f
     l = l - (h - p);
 }
 
+// ------------------------------------------------------------------ Eq. 3
+// Per atom, right after its coordination number (fused into the CN pass): the
+// exponents -k3 (n - nref_a)^2 minus their maximum are formed in FP64 (their
+// absolute error sets the relative error of the weights), and exp(y) is taken
+// as exp(y_hi) (1 + y_lo).  dW_a/dn is written as
+// -2 k3 W_a sum_b W_b (nref_b - nref_a), which has no cancellation against n.
+// Rows are padded to RP (4 or 8) and stored 4 values at a time.
+template <class T>
+__device__ __forceinline__ void store_row(T* dst, const T (&v)[8], int rp) {
+    using T4 = typename Real<sizeof(T) == 4>::T4;
+    T4* d = reinterpret_cast<T4*>(dst);
+    d[0] = T4{v[0], v[1], v[2], v[3]};
+    if (rp > 4) d[1] = T4{v[4], v[5], v[6], v[7]};
+}
+
+template <bool MIXED, int R>
+__device__ __forceinline__ void weights_atom(const Work& w, const Consts& c, const double* __restrict__ cnref,
+                                             const int* __restrict__ nref,
+                                             const typename Real<MIXED>::T* __restrict__ c6, int64_t p, int t,
+                                             double n) {
+    using T = typename Real<MIXED>::T;
+    const int nr = nref[t];
+    double cr[R], x[R];
+    double xmax = -1e300;
+#pragma unroll
+    for (int a = 0; a < R; ++a) {
+        cr[a] = cnref[t * R + a];
+        const double z = n - cr[a];
+        x[a] = -c.k3 * z * z;
+        if (a < nr && x[a] > xmax) xmax = x[a];
+    }
+    T L[R];
+    T sum = 0;
+#pragma unroll
+    for (int a = 0; a < R; ++a) {
+        if (a < nr) {
+            const double y = x[a] - xmax;
+            if constexpr (MIXED) {
+                const float yh = (float)y, yl = (float)(y - (double)yh);
+                L[a] = expf(yh) * (1.0f + yl);
+            } else {
+                L[a] = exp(y);
+            }
+        } else {
+            L[a] = 0;
+        }
+        sum += L[a];
+    }
+    const T inv = (T)1 / sum;
+#pragma unroll
+    for (int a = 0; a < R; ++a) L[a] *= inv;
+    T Wr[8], dWr[8];
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+        if (a < R) {
+            T s = 0;
+#pragma unroll
+            for (int b = 0; b < R; ++b) s += L[b] * (T)(cr[b] - cr[a]);
+            Wr[a] = L[a];
+            dWr[a] = -2 * (T)c.k3 * L[a] * s;
+        } else {
+            Wr[a] = dWr[a] = 0;
+        }
+    }
+    store_row<T>((T*)w.W + p * c.RP, Wr, c.RP);
+    store_row<T>((T*)w.dW + p * c.RP, dWr, c.RP);
+    T* vp = (T*)w.v + p * c.T * c.RP;
+    for (int u = 0; u < c.T; ++u) {
+        const T* cu = c6 + ((size_t)(u * c.T + t) * R) * R;  // C6ref[u][t][a][b]
+        T vr[8];
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+            T s = 0;
+            if (a < R) {
+#pragma unroll
+                for (int b = 0; b < R; ++b) s += cu[a * R + b] * L[b];
+            }
+            vr[a] = s;
+        }
+        store_row<T>(vp + u * c.RP, vr, c.RP);
+    }
+}
+
 // ------------------------------------------------------------------ Eq. 4
 // The coordination numbers feed dC6/dn, which can be large, so the mixed form
 // keeps n_i accurate to a few 1e-8: the pair vector is exact (D + e), r^2 is
 // formed in double-single, the argument k1 (rc/r - 1) is evaluated as
 // k1 (rc^2 - r^2) / (r (rc + r)) so its error is relative to its own size,
 // and the sum over neighbours is compensated.
-template <bool MIXED>
+template <bool MIXED, int R>
 __global__ void __launch_bounds__(128) k_cn(Work w, Consts c, const float4* __restrict__ rcpair,
-                                           const float2* __restrict__ exptab) {
+                                           const float2* __restrict__ exptab, const double* __restrict__ cnref,
+                                           const int* __restrict__ nref,
+                                           const typename Real<MIXED>::T* __restrict__ c6) {
     using T = typename Real<MIXED>::T;
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= w.Nr) return;
@@ -314,7 +400,9 @@ __global__ void __launch_bounds__(128) k_cn(Work w, Consts c, const float4* __re
                 nl += z.fl;
             }
         });
-        w.cn[p] = (double)nint + (double)nh + (double)nl;
+        const double n = (double)nint + (double)nh + (double)nl;
+        w.cn[p] = n;
+        weights_atom<MIXED, R>(w, c, cnref, nref, c6, p, S.tsrc() & 15, n);
     } else {
         const T rki = S.rk();
         LV.for_each(0, cnt, [&](int q) {
@@ -327,74 +415,7 @@ __global__ void __launch_bounds__(128) k_cn(Work w, Consts c, const float4* __re
             nh += f;
         });
         w.cn[p] = (double)nh;
-    }
-}
-
-// ------------------------------------------------------------------ Eq. 3
-// Per atom: the exponents -k3 (n - nref_a)^2 minus their maximum are formed in
-// FP64 (their absolute error sets the relative error of the weights), and
-// exp(y) is taken as exp(y_hi) (1 + y_lo).  dW_a/dn is written as
-// -2 k3 W_a sum_b W_b (nref_b - nref_a), which has no cancellation against n.
-template <bool MIXED, int R>
-__global__ void __launch_bounds__(128) k_weights(Work w, Consts c, const double* __restrict__ cnref,
-                                                 const int* __restrict__ nref,
-                                                 const typename Real<MIXED>::T* __restrict__ c6) {
-    using T = typename Real<MIXED>::T;
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= w.Nr) return;
-    const int t = rec_tsrc(w, p) & 15;
-    const double n = w.cn[p];
-    const int nr = nref[t];
-    double x[R];
-    double xmax = -1e300;
-#pragma unroll
-    for (int a = 0; a < R; ++a) {
-        const double z = n - cnref[t * R + a];
-        x[a] = -c.k3 * z * z;
-        if (a < nr && x[a] > xmax) xmax = x[a];
-    }
-    T L[R];
-    T sum = 0;
-#pragma unroll
-    for (int a = 0; a < R; ++a) {
-        if (a < nr) {
-            const double y = x[a] - xmax;
-            if constexpr (MIXED) {
-                const float yh = (float)y, yl = (float)(y - (double)yh);
-                L[a] = expf(yh) * (1.0f + yl);
-            } else {
-                L[a] = exp(y);
-            }
-        } else {
-            L[a] = 0;
-        }
-        sum += L[a];
-    }
-    const T inv = (T)1 / sum;
-#pragma unroll
-    for (int a = 0; a < R; ++a) L[a] *= inv;
-    T* Wp = (T*)w.W + p * c.RP;
-    T* dWp = (T*)w.dW + p * c.RP;
-#pragma unroll
-    for (int a = 0; a < R; ++a) {
-        T s = 0;
-#pragma unroll
-        for (int b = 0; b < R; ++b) s += L[b] * (T)(cnref[t * R + b] - cnref[t * R + a]);
-        Wp[a] = L[a];
-        dWp[a] = -2 * (T)c.k3 * L[a] * s;
-    }
-    for (int a = R; a < c.RP; ++a) Wp[a] = dWp[a] = 0;
-    T* vp = (T*)w.v + p * c.T * c.RP;
-    for (int u = 0; u < c.T; ++u) {
-        const T* cu = c6 + ((size_t)(u * c.T + t) * R) * R;  // C6ref[u][t][a][b]
-#pragma unroll
-        for (int a = 0; a < R; ++a) {
-            T s = 0;
-#pragma unroll
-            for (int b = 0; b < R; ++b) s += cu[a * R + b] * L[b];
-            vp[u * c.RP + a] = s;
-        }
-        for (int a = R; a < c.RP; ++a) vp[u * c.RP + a] = 0;
+        weights_atom<MIXED, R>(w, c, cnref, nref, c6, p, S.tsrc() & 15, (double)nh);
     }
 }
 
@@ -683,9 +704,9 @@ cudaError_t forward_impl(const Work& w, const Consts& c, const Tabs& tb, double*
         if (marks) cudaEventRecord(marks[k], st);
     };
     mark(0);
-    if (w.Nr > 0) k_cn<MIXED><<<nblk(w.Nr, TB), TB, 0, st>>>(w, c, tb.rcpair, tb.exptab);
-    mark(1);
-    if (w.Nr > 0) k_weights<MIXED, R><<<nblk(w.Nr, TB), TB, 0, st>>>(w, c, tb.cnref, tb.nref, (const T*)tb.c6);
+    if (w.Nr > 0)
+        k_cn<MIXED, R><<<nblk(w.Nr, TB), TB, 0, st>>>(w, c, tb.rcpair, tb.exptab, tb.cnref, tb.nref, (const T*)tb.c6);
+    mark(1);  // the weights (Eq. 3) are formed inside the CN pass
     mark(2);
     if (w.Nr > 0) {
         if (w_atom)

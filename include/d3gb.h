@@ -104,6 +104,15 @@ void d3_destroy(d3_handle *h);
  * Takes effect for work enqueued afterwards on the handle's last stream. */
 d3_status d3_set_damping(d3_handle *h, double s6, double s8, double a1, double a2_bohr);
 
+/* Graph replay (default on): after the first call for a geometry, a compute
+ * call whose pointers and parameters match the previous one is replayed as one
+ * CUDA graph (captured once on an internal stream, launched on the caller's
+ * stream), which removes the per-kernel launch overhead.  Calls made while
+ * profiling (d3_profile_enable) or while the caller's stream is being captured
+ * enqueue their kernels directly.  on = 0 always enqueues directly.  Results
+ * are identical either way. */
+d3_status d3_set_graphs(d3_handle *h, int32_t on);
+
 /* Accumulate mode for the NEP-D3 sum of Eq. 9 (U = U_NEP + U_D3, Sec. II A):
  * with on != 0, the compute calls ADD their E, F and W into the caller's
  * output arrays (which then hold, e.g., the short-range model's values)

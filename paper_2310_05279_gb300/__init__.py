@@ -216,6 +216,10 @@ class D3:
     def sync_status(self):
         self._check(self.lib.d3_sync_status(self.h))
 
+    def set_graphs(self, on: bool = True):
+        """Replay repeated compute calls as one CUDA graph (default on)."""
+        self._check(self.lib.d3_set_graphs(self.h, 1 if on else 0))
+
     def set_accumulate(self, on: bool = True):
         """Add E, F, W into the output tensors instead of overwriting them (Eq. 9 coupling)."""
         self._check(self.lib.d3_set_accumulate(self.h, 1 if on else 0))

@@ -104,6 +104,13 @@ struct d3_handle {
     int64_t prof_calls[6] = {0, 0, 0, 0, 0, 0};
     int64_t launches = 0;
     bool accumulate = false;  // d3_set_accumulate
+    // replay of the steady-state call as one CUDA graph (captured on cap_stream)
+    bool graphs = true;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    int64_t glaunches = 0;         // kernels in the captured call
+    const void* gkey[10] = {};     // pointers and generations the graph was captured with
+    int64_t plan_gen = 0, param_gen = 0;
 };
 
 namespace {
@@ -256,6 +263,7 @@ d3_status plan_geometry(d3_handle* h, Plan& P, int32_t B, const int64_t* offsets
 
 // (Re)allocate every device buffer of the plan for the current capacities.
 d3_status plan_alloc(d3_handle* h, Plan& P) {
+    ++h->plan_gen;  // a captured graph refers to the old buffers
     P.mem.release();
     P.bwd_scratch = nullptr;
     P.bwd_scratch_n = 0;
@@ -507,6 +515,70 @@ d3_status forward(d3_handle* h, int32_t B, const int64_t* offsets, const double*
     return D3_OK;
 }
 
+// The steady-state call (sized plan, no profiling) is the same sequence of
+// kernels and memsets every time for the same pointers and parameters, so it
+// is captured once as a CUDA graph on an internal stream and then replayed on
+// the caller's stream with one launch.  Calls made while the caller's stream
+// is itself being captured enqueue directly.
+bool graph_key_match(const d3_handle* h, const void* const (&k)[10]) {
+    if (!h->gexec) return false;
+    for (int i = 0; i < 10; ++i)
+        if (h->gkey[i] != k[i]) return false;
+    return true;
+}
+
+d3_status forward_graph(d3_handle* h, int32_t B, const int64_t* offsets, const double* pos, const int32_t* types,
+                        const double* cells, const int32_t* pbc, double* E, double* F, double* W, double* e_atom,
+                        double* cn, cudaStream_t st, double* w_atom) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    const bool direct = !h->graphs || h->prof_on || cudaStreamIsCapturing(st, &cs) != cudaSuccess ||
+                        cs != cudaStreamCaptureStatusNone;
+    if (direct || B <= 0 || !offsets || offsets[B] <= 0)
+        return forward(h, B, offsets, pos, types, cells, pbc, E, F, W, e_atom, cn, st, w_atom);
+    d3_status s = check_batch_args(h, B, offsets, pos, types, cells, pbc);
+    if (s != D3_OK) return s;
+    if (!E || !W || !F) return fail(h, D3_ERR_ARG, "NULL E, F or W");
+    s = ensure_plan(h, B, offsets, pos, types, cells, pbc, st);
+    if (s != D3_OK) return s;
+    h->last_stream = st;
+    const void* key[10] = {pos, types, E, F, W, e_atom, cn, w_atom, (const void*)(intptr_t)h->plan_gen,
+                           (const void*)(intptr_t)(h->param_gen * 2 + (h->accumulate ? 1 : 0))};
+    if (!graph_key_match(h, key)) {
+        if (!h->cap_stream && cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+            h->graphs = false;
+            return forward(h, B, offsets, pos, types, cells, pbc, E, F, W, e_atom, cn, st, w_atom);
+        }
+        // the captured work must start after everything already on the caller's stream
+        cudaGraph_t g = nullptr;
+        const int64_t before = h->launches;
+        cudaError_t e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            s = forward(h, B, offsets, pos, types, cells, pbc, E, F, W, e_atom, cn, h->cap_stream, w_atom);
+            e = cudaStreamEndCapture(h->cap_stream, &g);
+        }
+        const int64_t captured = h->launches - before;
+        h->launches = before;
+        h->last_stream = st;
+        cudaGraphExec_t x = nullptr;
+        if (e == cudaSuccess && s == D3_OK && g) e = cudaGraphInstantiate(&x, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e != cudaSuccess || s != D3_OK || !x) {
+            cudaGetLastError();
+            if (x) cudaGraphExecDestroy(x);
+            h->graphs = false;  // fall back to direct enqueueing for this handle
+            return forward(h, B, offsets, pos, types, cells, pbc, E, F, W, e_atom, cn, st, w_atom);
+        }
+        if (h->gexec) cudaGraphExecDestroy(h->gexec);
+        h->gexec = x;
+        h->glaunches = captured;
+        for (int i = 0; i < 10; ++i) h->gkey[i] = key[i];
+    }
+    cudaError_t e = cudaGraphLaunch(h->gexec, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "graph launch");
+    h->launches += h->glaunches;
+    return D3_OK;
+}
+
 }  // namespace
 
 // ====================================================================== C ABI
@@ -617,6 +689,8 @@ void d3_destroy(d3_handle* h) {
     for (auto& v : h->ev_pending)
         for (cudaEvent_t e : v) cudaEventDestroy(e);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     h->plan.mem.release();
     h->stage.release();
     h->tabmem.release();
@@ -632,7 +706,14 @@ d3_status d3_set_damping(d3_handle* h, double s6, double s8, double a1, double a
     h->prm.s8 = s8;
     h->prm.a1 = a1;
     h->prm.a2_bohr = a2_bohr;
+    ++h->param_gen;  // the damping parameters are kernel arguments of a captured graph
     return upload_pair_table(h);
+}
+
+d3_status d3_set_graphs(d3_handle* h, int32_t on) {
+    if (!h) return D3_ERR_ARG;
+    h->graphs = on != 0;
+    return D3_OK;
 }
 
 d3_status d3_set_accumulate(d3_handle* h, int32_t on) {
@@ -660,14 +741,14 @@ d3_status d3_build_neighbors(d3_handle* h, int32_t B, const int64_t* offsets, co
 d3_status d3_compute_batch_ex(d3_handle* h, int32_t B, const int64_t* offsets, const double* pos,
                               const int32_t* types, const double* cells, const int32_t* pbc, double* E, double* F,
                               double* W, double* e_atom, double* cn, void* stream) {
-    return forward(h, B, offsets, pos, types, cells, pbc, E, F, W, e_atom, cn, (cudaStream_t)stream);
+    return forward_graph(h, B, offsets, pos, types, cells, pbc, E, F, W, e_atom, cn, (cudaStream_t)stream, nullptr);
 }
 
 d3_status d3_compute_batch_atoms(d3_handle* h, int32_t B, const int64_t* offsets, const double* pos,
                                  const int32_t* types, const double* cells, const int32_t* pbc, double* E,
                                  double* F, double* W, double* e_atom, double* cn, double* w_atom, void* stream) {
     if (h && B > 0 && offsets && offsets[B] > 0 && !w_atom) return fail(h, D3_ERR_ARG, "NULL w_atom");
-    return forward(h, B, offsets, pos, types, cells, pbc, E, F, W, e_atom, cn, (cudaStream_t)stream, w_atom);
+    return forward_graph(h, B, offsets, pos, types, cells, pbc, E, F, W, e_atom, cn, (cudaStream_t)stream, w_atom);
 }
 
 d3_status d3_heat_current(int64_t n, const double* w_atom, const double* vel, double* J, void* stream) {
@@ -678,7 +759,8 @@ d3_status d3_heat_current(int64_t n, const double* w_atom, const double* vel, do
 d3_status d3_compute_batch(d3_handle* h, int32_t B, const int64_t* offsets, const double* pos,
                            const int32_t* types, const double* cells, const int32_t* pbc, double* E, double* F,
                            double* W, void* stream) {
-    return forward(h, B, offsets, pos, types, cells, pbc, E, F, W, nullptr, nullptr, (cudaStream_t)stream);
+    return forward_graph(h, B, offsets, pos, types, cells, pbc, E, F, W, nullptr, nullptr, (cudaStream_t)stream,
+                         nullptr);
 }
 
 d3_status d3_compute(d3_handle* h, const double* pos, const int32_t* types, int64_t n, const double* cell,
@@ -686,7 +768,7 @@ d3_status d3_compute(d3_handle* h, const double* pos, const int32_t* types, int6
     if (!h) return D3_ERR_ARG;
     if (n < 0 || !cell || !pbc) return fail(h, D3_ERR_ARG, "bad structure description");
     const int64_t off[2] = {0, n};
-    return forward(h, 1, off, pos, types, cell, pbc, E, F, W, nullptr, nullptr, (cudaStream_t)stream);
+    return forward_graph(h, 1, off, pos, types, cell, pbc, E, F, W, nullptr, nullptr, (cudaStream_t)stream, nullptr);
 }
 
 d3_status d3_compute_batch_host(d3_handle* h, int32_t B, const int64_t* offsets, const double* pos,
@@ -715,7 +797,8 @@ d3_status d3_compute_batch_host(d3_handle* h, int32_t B, const int64_t* offsets,
     cudaError_t e = cudaMemcpyAsync(h->s_pos, pos, 3 * N * sizeof(double), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h->s_types, types, N * sizeof(int32_t), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_fail(h, e, "input copy");
-    s = forward(h, B, offsets, h->s_pos, h->s_types, cells, pbc, h->s_E, h->s_F, h->s_W, nullptr, nullptr, st);
+    s = forward_graph(h, B, offsets, h->s_pos, h->s_types, cells, pbc, h->s_E, h->s_F, h->s_W, nullptr, nullptr, st,
+                      nullptr);
     if (s != D3_OK) return s;
     e = cudaMemcpyAsync(E, h->s_E, B * sizeof(double), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(F, h->s_F, 3 * N * sizeof(double), cudaMemcpyDeviceToHost, st);

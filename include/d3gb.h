@@ -185,8 +185,11 @@ d3_status d3_compute_batch_host(d3_handle *h, int32_t B, const int64_t *offsets,
  *   dLdpos     device double[N][3] = dL/dx (per A), input order
  * The force term needs the Hessian-vector product H*(dL/dF); it is formed by
  * forward-mode differentiation of the whole force evaluation along dL/dF
- * (coordination numbers recomputed, no per-pair storage), in FP64.
- * Either output may be NULL.  Inputs as in d3_compute_batch. */
+ * (coordination numbers recomputed, no per-pair storage).  The coordination
+ * numbers, weights and chain rule are in FP64; the dispersion pair terms are
+ * FP64 for a D3_FP64 handle and FP32 dual numbers with FP64 partial sums for
+ * a D3_MIXED handle (several times faster, same relative precision as the
+ * mixed forward).  Either output may be NULL.  Inputs as in d3_compute_batch. */
 d3_status d3_backward(d3_handle *h, int32_t B, const int64_t *offsets, const double *pos, const int32_t *types,
                       const double *cells, const int32_t *pbc, const double *dLdE, const double *dLdF,
                       double *dLdparams, double *dLdpos, void *stream);

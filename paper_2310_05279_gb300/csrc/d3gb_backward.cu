@@ -1,4 +1,7 @@
 // d3gb_backward.cu -- hand-written backward of (E, F) for damping refits.
+// The handle's precision selects the dispersion pass of the backward: FP64
+// dual numbers, or (mixed form) FP32 dual numbers on split positions with FP64
+// partial sums; the CN, weight and chain passes are FP64 in both.
 //
 // For a loss L(E, F) with upstream gradients gE = dL/dE (per structure) and
 // gF = dL/dF (per atom):
@@ -56,6 +59,10 @@ struct BW {
     Dual* th;     // [Nr][4] dE_i/d(s6, s8, a1, a2), half pair sums
     double* xd;   // [(Nr + ghost_cap) * 3] tangent positions (bohr)
     double* sth;  // [B][8] per-structure dE/dtheta (value, tangent)
+    // mixed form of the dispersion pass
+    float* vf;    // [Nr][T][2 * RP]: R values of v padded to RP, then R tangents padded to RP
+    float4* xdf;  // [Nr + ghost_cap] tangent positions as FP32
+    int RP;
 };
 
 __host__ __device__ inline BW carve(double* s, int64_t Nr, int64_t Ng, int T, int R, int B) {
@@ -79,6 +86,12 @@ __host__ __device__ inline BW carve(double* s, int64_t Nr, int64_t Ng, int T, in
     b.xd = x;
     x += 3 * (Nr + Ng);
     b.sth = x;
+    x += 8 * (int64_t)B;
+    b.RP = R <= 4 ? 4 : 8;
+    x += (4 - ((reinterpret_cast<uintptr_t>(x) / sizeof(double)) & 3)) & 3;  // 32-byte alignment
+    b.vf = reinterpret_cast<float*>(x);
+    x += Nr * T * b.RP;
+    b.xdf = reinterpret_cast<float4*>(x);
     return b;
 }
 
@@ -93,8 +106,13 @@ __global__ void kb_xdot(Work w, BW b, const double* __restrict__ gF, int64_t nt)
     if (q >= nt || q >= w.Nr + w.start_ghost[w.ncells]) return;
     const int src = rec_tsrc(w, q) >> 4;
     const int i = w.perm[src];
+    double t[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) b.xd[3 * q + a] = gF[3 * (int64_t)i + a] * (1.0 / kBohrA);
+    for (int a = 0; a < 3; ++a) {
+        t[a] = gF[3 * (int64_t)i + a] * (1.0 / kBohrA);
+        b.xd[3 * q + a] = t[a];
+    }
+    b.xdf[q] = make_float4((float)t[0], (float)t[1], (float)t[2], 0.0f);
 }
 
 __device__ __forceinline__ void ddist(const Work& w, const BW& b, int64_t p, int64_t q, Dual (&d)[3], Dual& r2) {
@@ -167,6 +185,12 @@ __global__ void kb_weights(Work w, BW b, BConsts c, const double* __restrict__ c
 #pragma unroll
             for (int bb = 0; bb < R; ++bb) s += cu[a * R + bb] * L[bb];
             b.v[(p * c.T + u) * R + a] = s;
+            b.vf[(p * c.T + u) * 2 * b.RP + a] = (float)s.v;
+            b.vf[(p * c.T + u) * 2 * b.RP + b.RP + a] = (float)s.t;
+        }
+        for (int a = R; a < b.RP; ++a) {
+            b.vf[(p * c.T + u) * 2 * b.RP + a] = 0.0f;
+            b.vf[(p * c.T + u) * 2 * b.RP + b.RP + a] = 0.0f;
         }
     }
 }
@@ -223,6 +247,134 @@ __global__ void kb_disp(Work w, BW b, BConsts c, const dbl4* __restrict__ pairb)
     for (int a = 0; a < 3; ++a) b.F[3 * p + a] = F[a];
 #pragma unroll
     for (int m = 0; m < 4; ++m) b.th[4 * p + m] = 0.5 * th[m];
+}
+
+// ---- mixed form of the dispersion pass of the backward: the same dual-number
+// evaluation with FP32 pair arithmetic on the split positions (hi + lo) and
+// FP32 tangents, FP32 partial sums promoted to FP64 every kChunk pairs and a
+// compensated value part of dE/dn (it scales the chain-rule forces).
+struct DF {
+    float v, t;
+};
+__device__ __forceinline__ DF operator+(DF a, DF b) { return DF{a.v + b.v, a.t + b.t}; }
+__device__ __forceinline__ DF operator*(DF a, DF b) { return DF{a.v * b.v, fmaf(a.v, b.t, a.t * b.v)}; }
+__device__ __forceinline__ DF operator*(float s, DF a) { return DF{s * a.v, s * a.t}; }
+__device__ __forceinline__ DF finv(DF a) {
+    const float r = 1.0f / a.v;
+    return DF{r, -a.t * r * r};
+}
+__device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+template <int R>
+__global__ void __launch_bounds__(128) kb_disp_mixed(Work w, BW b, BConsts c, const dbl4* __restrict__ pairb) {
+    // per element pair: R^6, R^8, s8 R0^2, R0, 6 s6 R^4 R, 8 s8 R0^2 R^6 R, R0^2
+    __shared__ float tab[kMaxTypes * kMaxTypes][8];
+    for (int k = threadIdx.x; k < c.T * c.T; k += blockDim.x) {
+        const dbl4 pb = pairb[k];
+        const double Rd = pb.y, R2 = Rd * Rd, R4 = R2 * R2, R6 = R4 * R2, R8 = R4 * R4;
+        tab[k][0] = (float)R6;
+        tab[k][1] = (float)R8;
+        tab[k][2] = (float)(c.s8 * pb.z);
+        tab[k][3] = (float)pb.x;
+        tab[k][4] = (float)(6.0 * c.s6 * R4 * Rd);
+        tab[k][5] = (float)(8.0 * c.s8 * pb.z * R6 * Rd);
+        tab[k][6] = (float)pb.z;
+        tab[k][7] = 0.0f;
+    }
+    __syncthreads();
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= w.Nr) return;
+    float4 hp, lp;
+    rec_load(w, p, hp, lp);
+    const int ti = __float_as_int(hp.w) & 15;
+    const float4 tp = b.xdf[p];
+    DF Wi[R], dWi[R];
+#pragma unroll
+    for (int a = 0; a < R; ++a) {
+        const Dual x = b.W[p * R + a], y = b.dW[p * R + a];
+        Wi[a] = DF{(float)x.v, (float)x.t};
+        dWi[a] = DF{(float)y.v, (float)y.t};
+    }
+    const StructGeo& G = w.geo[w.sid[p]];
+    const ListView LV{w.nbr_disp + list_row(G.list_base_disp, p - G.atom_base, G.cap_disp)};
+    const int cnt = w.cnt_disp[p];
+    const float rc2f = (float)c.rc_disp2, s6 = (float)c.s6;
+    const int stride = c.T * 2 * b.RP;
+    float dnh = 0.0f, dnl = 0.0f;
+    double dnt = 0.0, Fv[3] = {0, 0, 0}, Ft[3] = {0, 0, 0}, thv[4] = {0, 0, 0, 0}, tht[4] = {0, 0, 0, 0};
+    for (int k0 = 0; k0 < cnt; k0 += kChunk) {
+        const int k1e = min(cnt, k0 + kChunk);
+        float dt = 0.0f, fv[3] = {0, 0, 0}, ft[3] = {0, 0, 0}, hv[4] = {0, 0, 0, 0}, ht[4] = {0, 0, 0, 0};
+        LV.for_each(k0, k1e, [&](int q) {
+            float4 hq, lq;
+            rec_load(w, q, hq, lq);
+            const float dx = (hq.x - hp.x) + (lq.x - lp.x), dy = (hq.y - hp.y) + (lq.y - lp.y),
+                        dz = (hq.z - hp.z) + (lq.z - lp.z);
+            const float r2v = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            bool in;
+            if (fabsf(r2v - rc2f) > 4e-6f * rc2f) {
+                in = r2v < rc2f;
+            } else {  // within the FP32 error band of the cutoff: decide in FP64
+                const dbl4 x = w.pos64[p], y = w.pos64[q];
+                const double ex = y.x - x.x, ey = y.y - x.y, ez = y.z - x.z;
+                in = ex * ex + ey * ey + ez * ez < c.rc_disp2;
+            }
+            if (!in) return;
+            const int tsq = __float_as_int(hq.w);
+            const float4 tq = b.xdf[q];
+            const float ux = tq.x - tp.x, uy = tq.y - tp.y, uz = tq.z - tp.z;
+            const DF r2 = DF{r2v, 2.0f * fmaf(dx, ux, fmaf(dy, uy, dz * uz))};
+            const float* tb = tab[ti * c.T + (tsq & 15)];
+            const float* vq = b.vf + (int64_t)(tsq >> 4) * stride + ti * 2 * b.RP;
+            DF C6 = DF{0.0f, 0.0f}, dC6 = DF{0.0f, 0.0f};
+#pragma unroll
+            for (int a = 0; a < R; ++a) {
+                const DF v = DF{vq[a], vq[b.RP + a]};
+                C6 = C6 + Wi[a] * v;
+                dC6 = dC6 + dWi[a] * v;
+            }
+            const DF r4 = r2 * r2, r6 = r4 * r2, r8 = r4 * r4;
+            const DF i6 = finv(DF{r6.v + tb[0], r6.t}), i8 = finv(DF{r8.v + tb[1], r8.t});
+            const DF t6 = s6 * i6, t8 = tb[2] * i8;
+            const DF g = t6 + t8;
+            const DF gd = g * dC6;
+            float s, e;
+            two_sum_f(dnh, -gd.v, s, e);
+            dnh = s;
+            dnl += e;
+            dt -= gd.t;
+            const DF fc = C6 * (6.0f * (r4 * (t6 * i6)) + 8.0f * (r6 * (t8 * i8)));
+            fv[0] = fmaf(fc.v, dx, fv[0]); fv[1] = fmaf(fc.v, dy, fv[1]); fv[2] = fmaf(fc.v, dz, fv[2]);
+            ft[0] += fmaf(fc.t, dx, fc.v * ux); ft[1] += fmaf(fc.t, dy, fc.v * uy); ft[2] += fmaf(fc.t, dz, fc.v * uz);
+            // derivatives of this ordered instance's energy -C6 g in s6, s8, a1, a2 (halved at the end)
+            const DF e6 = C6 * i6, e8 = C6 * i8;
+            hv[0] -= e6.v; ht[0] -= e6.t;
+            hv[1] = fmaf(-tb[6], e8.v, hv[1]); ht[1] = fmaf(-tb[6], e8.t, ht[1]);
+            const DF dR = C6 * (tb[4] * (i6 * i6) + tb[5] * (i8 * i8));
+            hv[2] = fmaf(tb[3], dR.v, hv[2]); ht[2] = fmaf(tb[3], dR.t, ht[2]);
+            hv[3] += dR.v; ht[3] += dR.t;
+        });
+        dnt += (double)dt;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            Fv[a] += (double)fv[a];
+            Ft[a] += (double)ft[a];
+        }
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            thv[m] += (double)hv[m];
+            tht[m] += (double)ht[m];
+        }
+    }
+    b.dEdn[p] = Dual{(double)dnh + (double)dnl, dnt};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) b.F[3 * p + a] = Dual{Fv[a], Ft[a]};
+#pragma unroll
+    for (int m = 0; m < 4; ++m) b.th[4 * p + m] = Dual{0.5 * thv[m], 0.5 * tht[m]};
 }
 
 __global__ void kb_chain(Work w, BW b, BConsts c, const double* __restrict__ gE, double* __restrict__ dLdx) {
@@ -309,7 +461,7 @@ inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 template <int R>
 cudaError_t backward_impl(const Work& w, const Consts& cc, const double* c6d, const dbl4* pairb, const double* cnref,
                           const int* nref, const double* gE, const double* gF, double* dLdp, double* dLdx,
-                          double* scratch, int B, cudaStream_t st) {
+                          double* scratch, int B, bool mixed, cudaStream_t st) {
     BW b = carve(scratch, w.Nr, w.ghost_cap, w.T, R, B);
     BConsts c{cc.rc_disp2, cc.rc_cn2, cc.k1, cc.k3, cc.s6, cc.s8, cc.T, R};
     const int TB = 128;
@@ -318,7 +470,10 @@ cudaError_t backward_impl(const Work& w, const Consts& cc, const double* c6d, co
         kb_xdot<<<nblk(w.Nr + w.ghost_cap, TB), TB, 0, st>>>(w, b, gF, w.Nr + w.ghost_cap);
         kb_cn<<<nblk(w.Nr, TB), TB, 0, st>>>(w, b, c);
         kb_weights<R><<<nblk(w.Nr, TB), TB, 0, st>>>(w, b, c, cnref, nref, c6d);
-        kb_disp<R><<<nblk(w.Nr, TB), TB, 0, st>>>(w, b, c, pairb);
+        if (mixed)
+            kb_disp_mixed<R><<<nblk(w.Nr, TB), TB, 0, st>>>(w, b, c, pairb);
+        else
+            kb_disp<R><<<nblk(w.Nr, TB), TB, 0, st>>>(w, b, c, pairb);
         kb_chain<<<nblk(w.Nr, TB), TB, 0, st>>>(w, b, c, gE, dLdx);
     }
     kb_struct_sum<<<B, 256, 0, st>>>(w, b);
@@ -331,13 +486,16 @@ cudaError_t backward_impl(const Work& w, const Consts& cc, const double* c6d, co
 int64_t backward_scratch_doubles(const Work& w, int B) {
     const int64_t Nr = w.Nr, Ng = w.ghost_cap;
     const int64_t duals = Nr * (1 + 2 * (int64_t)w.R + (int64_t)w.T * w.R + 1 + 3 + 4);
-    return 2 * duals + 3 * (Nr + Ng) + 8 * (int64_t)B + 64;
+    const int64_t rp = w.R <= 4 ? 4 : 8;
+    // duals, tangent positions, per-structure sums, FP32 v rows and tangents (+ alignment)
+    return 2 * duals + 3 * (Nr + Ng) + 8 * (int64_t)B + Nr * (int64_t)w.T * rp + 2 * (Nr + Ng) + 64;
 }
 
 cudaError_t launch_backward(const Work& w, const Consts& c, const double* c6d, const dbl4* pairb,
                             const double* cnref, const int* nref, const double* dLdE, const double* dLdF,
-                            double* dLdp, double* dLdx, double* scratch, int B, cudaStream_t st) {
-#define D3_BWD(RR) return backward_impl<RR>(w, c, c6d, pairb, cnref, nref, dLdE, dLdF, dLdp, dLdx, scratch, B, st)
+                            double* dLdp, double* dLdx, double* scratch, int B, bool mixed, cudaStream_t st) {
+#define D3_BWD(RR) \
+    return backward_impl<RR>(w, c, c6d, pairb, cnref, nref, dLdE, dLdF, dLdp, dLdx, scratch, B, mixed, st)
     switch (c.R) {
         case 1: D3_BWD(1);
         case 2: D3_BWD(2);

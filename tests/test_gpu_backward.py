@@ -29,9 +29,9 @@ def oracle_loss(oracle_mod, b, prm, Et, Ft):
     return float(np.sum((r["E"] - Et) ** 2) + LAM * np.sum((r["F"] - Ft) ** 2)), r
 
 
-def gpu_grad(torch, b, prm, Et, Ft):
+def gpu_grad(torch, b, prm, Et, Ft, precision="fp64"):
     from paper_2310_05279_gb300 import D3
-    d3 = D3(b.tables, prm, precision="fp64")
+    d3 = D3(b.tables, prm, precision=precision)
     pos, typ = to_dev(b)
     out = d3.compute_batch(pos, typ, b.offsets, b.cells, b.pbc)
     gE = 2.0 * (out["E"] - torch.tensor(Et, device="cuda"))
@@ -41,10 +41,14 @@ def gpu_grad(torch, b, prm, Et, Ft):
     return g["dparams"].cpu().numpy(), g["dpos"].cpu().numpy()
 
 
-def test_param_gradient_vs_oracle(setup, oracle_mod):
+# The mixed backward's dispersion pass sums FP32 dual-number pair terms in FP64
+# chunks, like the forward: its gradients carry the forward's relative error
+# (~1e-7), well inside the tolerances below.
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_param_gradient_vs_oracle(setup, oracle_mod, precision):
     torch, b, Et, Ft = setup
     prm = dict(wl.PBE_BJ)
-    gp, _ = gpu_grad(torch, b, prm, Et, Ft)
+    gp, _ = gpu_grad(torch, b, prm, Et, Ft, precision)
     L0, r0 = oracle_loss(oracle_mod, b, prm, Et, Ft)
     gE = 2.0 * (r0["E"] - Et)
     gF = 2.0 * LAM * (r0["F"] - Ft)
@@ -64,10 +68,11 @@ def test_param_gradient_vs_oracle(setup, oracle_mod):
     np.testing.assert_allclose(gp, fd, rtol=1e-5, atol=1e-8 * np.abs(fd).max())
 
 
-def test_position_gradient_vs_fd(setup, oracle_mod):
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_position_gradient_vs_fd(setup, oracle_mod, precision):
     torch, b, Et, Ft = setup
     prm = dict(wl.PBE_BJ)
-    _, gx = gpu_grad(torch, b, prm, Et, Ft)
+    _, gx = gpu_grad(torch, b, prm, Et, Ft, precision)
     g = np.random.Generator(np.random.PCG64(2))
     idx = g.choice(b.natoms, 8, replace=False)
     for i in idx:
@@ -98,3 +103,24 @@ def test_autograd_function(setup, oracle_mod):
     gp, gx = gpu_grad(torch, b, dict(wl.PBE_BJ), Et, Ft)
     np.testing.assert_allclose(theta.grad.cpu().numpy(), gp, rtol=1e-12, atol=1e-14)
     np.testing.assert_allclose(pos.grad.cpu().numpy(), gx, rtol=1e-12, atol=1e-14)
+
+
+def test_mixed_backward_vs_fp64_full_fit_batch(setup):
+    """The full 256-structure fit batch: mixed and FP64 backward on the same
+    upstream gradients agree to the forward's relative precision."""
+    torch = setup[0]
+    from paper_2310_05279_gb300 import D3
+    b = wl.fit_batch()
+    pos, typ = to_dev(b)
+    g = torch.Generator(device="cuda").manual_seed(0)
+    gE = torch.randn(b.nstruct, dtype=torch.float64, device="cuda", generator=g)
+    gF = 0.01 * torch.randn(b.natoms, 3, dtype=torch.float64, device="cuda", generator=g)
+    res = {}
+    for prec in ("fp64", "mixed"):
+        d3 = D3(b.tables, precision=prec)
+        r = d3.backward(pos, typ, b.offsets, b.cells, b.pbc, gE, gF)
+        d3.sync_status()
+        res[prec] = {k: v.cpu().numpy() for k, v in r.items()}
+    m, f = res["mixed"], res["fp64"]
+    assert np.all(np.abs(m["dparams"] - f["dparams"]) <= 1e-6 * np.abs(f["dparams"]))
+    assert np.abs(m["dpos"] - f["dpos"]).max() <= 1e-6 * np.abs(f["dpos"]).max()

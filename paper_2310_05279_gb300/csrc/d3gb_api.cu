@@ -509,7 +509,7 @@ d3_status forward(d3_handle* h, int32_t B, const int64_t* offsets, const double*
     cudaError_t e = launch_forward(P.w, c, mixed, tb, E, F, W, e_atom, cn, w_atom, B, st,
                                    ev.size() == 7 ? ev.data() + 1 : nullptr);
     if (e != cudaSuccess) return cuda_fail(h, e, "forward launch");
-    h->launches += (P.Nr > 0 ? kForwardLaunches - 1 : 1);
+    h->launches += (P.Nr > 0 ? kForwardLaunches : 1);
     if (ev.size() == 7) h->ev_pending.push_back(ev);
     else for (cudaEvent_t x : ev) h->ev_pool.push_back(x);
     return D3_OK;

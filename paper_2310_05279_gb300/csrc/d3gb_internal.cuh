@@ -216,6 +216,7 @@ cudaError_t launch_forward(const Work& w, const Consts& c, bool mixed, const Tab
                            cudaEvent_t* marks);
 // Eq. 8 per atom: J_i = W_i . v_i (device arrays).
 cudaError_t launch_heat(int64_t n, const double* w_atom, const double* vel, double* J, cudaStream_t st);
-constexpr int kForwardLaunches = 5;  // kernels per forward pass (B > 0, N > 0)
-constexpr int kBuildLaunches = 14;   // kernels per neighbour build (N > 0, with images)
+constexpr int kForwardLaunches = 5;  // kernels per forward pass (B > 0, N > 0): CN, dispersion, chain, 2 sums
+constexpr int kBuildLaunches = 15;   // kernels per neighbour build (N > 0): reset, wrap, images, 2 x 3 scan,
+                                     // 2 scatter, sort, 2 fill, lists
 }  // namespace d3gb

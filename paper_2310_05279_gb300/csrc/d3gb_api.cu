@@ -302,6 +302,8 @@ d3_status plan_alloc(d3_handle* h, Plan& P) {
     if (e == cudaSuccess) e = m.alloc((T**)&(ptr), (size_t)(n))
     A(dgeo, StructGeo, B);
     A(doff, int64_t, B + 1);
+    int* dsid = nullptr;
+    A(dsid, int, Nr);
     A(w.cnt_real, int, C + 1);
     A(w.cnt_ghost, int, C + 1);
     A(w.start_real, int, C + 1);
@@ -357,6 +359,7 @@ d3_status plan_alloc(d3_handle* h, Plan& P) {
     P.w.status = h->d_status;
     P.w.geo = dgeo;
     P.w.offsets = doff;
+    P.w.sid_in = dsid;
     const double rld = list_radius(h, h->prm.rc_disp_A), rln = list_radius(h, h->prm.rc_cn_A);
     w.rl_disp2 = (float)(rld * rld);
     w.rl_cn2 = (float)(rln * rln);
@@ -368,6 +371,12 @@ d3_status plan_alloc(d3_handle* h, Plan& P) {
     P.gate = gate;
     e = cudaMemcpy(dgeo, P.geo.data(), sizeof(StructGeo) * B, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(doff, P.offsets.data(), sizeof(int64_t) * (B + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && Nr > 0) {
+        std::vector<int> sid((size_t)Nr);
+        for (int s = 0; s < B; ++s)
+            for (int64_t i = P.offsets[s]; i < P.offsets[s + 1]; ++i) sid[(size_t)i] = s;
+        e = cudaMemcpy(dsid, sid.data(), sizeof(int) * (size_t)Nr, cudaMemcpyHostToDevice);
+    }
     if (e != cudaSuccess) return cuda_fail(h, e, "geometry upload");
     return D3_OK;
 }

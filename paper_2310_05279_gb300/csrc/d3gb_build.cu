@@ -40,7 +40,7 @@ __device__ inline int cell_id(const StructGeo& G, const double f[3]) {
 __global__ void __launch_bounds__(256) k_wrap(Work w, const double* __restrict__ pos, const int32_t* __restrict__ types) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= w.Nr || skip_build(w)) return;
-    const int s = struct_of(w.offsets, w.B, i);
+    const int s = w.sid_in[i];
     const StructGeo& G = w.geo[s];
     double xb[3];
     bool fin = true;
@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(256) k_images(Work w) {
     if (skip_build(w)) return;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool live = i < w.Nr;
-    const int s = live ? struct_of(w.offsets, w.B, i) : 0;
+    const int s = live ? w.sid_in[i] : 0;
     const StructGeo& G = w.geo[s];
     double f[3] = {0, 0, 0};
     int nlo[3] = {0, 0, 0}, nhi[3] = {0, 0, 0};
@@ -351,7 +351,7 @@ __global__ void k_fill_real(Work w, const int32_t* __restrict__ types, const dou
     int t = types[i];
     if (t < 0 || t >= w.T) t = 0;
     w.perm[p] = i;
-    w.sid[p] = struct_of(w.offsets, w.B, i);
+    w.sid[p] = w.sid_in[i];
     w.cell_sorted[p] = w.cell_of[i];
     w.slot_of[i] = (int)p;  // slot_of becomes the inverse permutation from here on
     const double x[3] = {w.xw[3 * i], w.xw[3 * i + 1], w.xw[3 * i + 2]};

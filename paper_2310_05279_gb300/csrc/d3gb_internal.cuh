@@ -64,6 +64,7 @@ struct StructGeo {
 struct Work {
     const StructGeo* geo;
     const int64_t* offsets;  // [B+1]
+    const int* sid_in;       // [Nr] structure of each atom in input order
     int B;
     int64_t Nr;              // real atoms
     int64_t ncells;          // total cells

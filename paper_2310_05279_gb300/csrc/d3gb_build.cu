@@ -253,37 +253,94 @@ __global__ void k_scatter_ghost(Work w) {
 }
 
 // Deterministic order inside each cell: real atoms by input index, images by
-// (source, translation).
-__global__ void k_sort_cells(Work w) {
-    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= w.ncells || skip_build(w)) return;
+// (source, translation).  A block takes 256 consecutive cells, whose atoms
+// form one contiguous slice of sorted slots: the slice is staged in shared
+// memory, each thread insertion-sorts its own cell there, and the slice is
+// written back.  A slice larger than the stage is sorted in place in global
+// memory instead.
+constexpr int kSortStage = 2048;
+
+__device__ __forceinline__ long long image_key(const Work& w, int g) {
+    return ((long long)w.ghost_src[g] << 24) | (long long)w.ghost_shift[g];
+}
+
+__global__ void __launch_bounds__(256) k_sort_cells(Work w) {
+    if (skip_build(w)) return;  // uniform over the grid
+    __shared__ int sr[kSortStage];
+    __shared__ int sg[kSortStage];
+    __shared__ long long sk[kSortStage];
+    const int64_t c0 = (int64_t)blockIdx.x * blockDim.x;
+    const int64_t c1 = c0 + blockDim.x < w.ncells ? c0 + blockDim.x : w.ncells;
+    const int64_t c = c0 + threadIdx.x;
+    const bool live = c < w.ncells;
     {
-        int b = w.start_real[c], e = w.start_real[c + 1];
-        for (int k = b + 1; k < e; ++k) {
-            int key = w.sorted_src[k];
-            int m = k - 1;
-            while (m >= b && w.sorted_src[m] > key) {
-                w.sorted_src[m + 1] = w.sorted_src[m];
-                --m;
+        const int lo = w.start_real[c0], hi = w.start_real[c1];
+        const bool fits = hi - lo <= kSortStage;
+        if (fits)
+            for (int k = lo + threadIdx.x; k < hi; k += blockDim.x) sr[k - lo] = w.sorted_src[k];
+        __syncthreads();
+        if (live) {
+            const int b = w.start_real[c], e = w.start_real[c + 1];
+            // slots [b, e) of the cell: in the stage at [b - lo, e - lo), else in place
+            int* v = fits ? sr : w.sorted_src;
+            const int o = fits ? lo : 0;
+            for (int k = b + 1 - o; k < e - o; ++k) {
+                const int key = v[k];
+                int m = k - 1;
+                while (m >= b - o && v[m] > key) {
+                    v[m + 1] = v[m];
+                    --m;
+                }
+                v[m + 1] = key;
             }
-            w.sorted_src[m + 1] = key;
         }
+        __syncthreads();
+        if (fits)
+            for (int k = lo + threadIdx.x; k < hi; k += blockDim.x) w.sorted_src[k] = sr[k - lo];
     }
     {
-        int b = w.start_ghost[c], e = w.start_ghost[c + 1];
-        for (int k = b + 1; k < e; ++k) {
-            int g = w.gsorted[k];
-            int64_t key = ((int64_t)w.ghost_src[g] << 24) | (int64_t)w.ghost_shift[g];
-            int m = k - 1;
-            while (m >= b) {
-                int h = w.gsorted[m];
-                int64_t kh = ((int64_t)w.ghost_src[h] << 24) | (int64_t)w.ghost_shift[h];
-                if (kh <= key) break;
-                w.gsorted[m + 1] = h;
-                --m;
+        const int lo = w.start_ghost[c0], hi = w.start_ghost[c1];
+        const bool fits = hi - lo <= kSortStage;
+        if (fits)
+            for (int k = lo + threadIdx.x; k < hi; k += blockDim.x) {
+                const int g = w.gsorted[k];
+                sg[k - lo] = g;
+                sk[k - lo] = image_key(w, g);
             }
-            w.gsorted[m + 1] = g;
+        __syncthreads();
+        if (live) {
+            const int b = w.start_ghost[c], e = w.start_ghost[c + 1];
+            if (fits) {
+                for (int k = b + 1 - lo; k < e - lo; ++k) {
+                    const int g = sg[k];
+                    const long long key = sk[k];
+                    int m = k - 1;
+                    while (m >= b - lo && sk[m] > key) {
+                        sk[m + 1] = sk[m];
+                        sg[m + 1] = sg[m];
+                        --m;
+                    }
+                    sk[m + 1] = key;
+                    sg[m + 1] = g;
+                }
+            } else {
+                for (int k = b + 1; k < e; ++k) {
+                    const int g = w.gsorted[k];
+                    const long long key = image_key(w, g);
+                    int m = k - 1;
+                    while (m >= b) {
+                        const int h = w.gsorted[m];
+                        if (image_key(w, h) <= key) break;
+                        w.gsorted[m + 1] = h;
+                        --m;
+                    }
+                    w.gsorted[m + 1] = g;
+                }
+            }
         }
+        __syncthreads();
+        if (fits)
+            for (int k = lo + threadIdx.x; k < hi; k += blockDim.x) w.gsorted[k] = sg[k - lo];
     }
 }
 

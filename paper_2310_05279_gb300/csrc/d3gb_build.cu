@@ -69,8 +69,10 @@ __global__ void __launch_bounds__(256) k_wrap(Work w, const double* __restrict__
     for (int a = 0; a < 3; ++a) {
         const double xw = f[0] * G.H[a] + f[1] * G.H[3 + a] + f[2] * G.H[6 + a];
         w.xw[3 * i + a] = xw;
-        w.xref[3 * i + a] = xb[a];
-        w.wshift[3 * i + a] = xw - xb[a];
+        if (w.skin_half2 > 0.0) {  // references for list reuse
+            w.xref[3 * i + a] = xb[a];
+            w.wshift[3 * i + a] = xw - xb[a];
+        }
     }
     const int cid = cell_id(G, f);
     w.cell_of[i] = cid;

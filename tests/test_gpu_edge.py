@@ -222,3 +222,46 @@ def test_internal_graph_replay(torch_cuda):
     d3.compute_batch(pos, typ, b.offsets, b.cells, b.pbc, out=out)
     d3.sync_status()
     assert torch.allclose(out["E"], 2 * r2["E"], rtol=1e-14, atol=0)
+
+
+def _limit_batch():
+    """16 element types with up to 7 references each (the table limits), on
+    periodic triclinic structures."""
+    g = np.random.Generator(np.random.PCG64(61))
+    names = [f"E{k}" for k in range(16)]
+    tabs = wl.random_tables(names, 62, max_ref=7, nref_max=7)
+    structs = []
+    for n in (90, 160, 240):
+        pos, _, cell, pbc = wl.random_structure(g, n, wl.UNEVEN_ELEMENTS)
+        structs.append((pos, g.integers(0, 16, n).astype(np.int32), cell, pbc))
+    return wl.batch_of(structs, tabs)
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_table_limits(torch_cuda, oracle_mod, precision):
+    b = _limit_batch()
+    assert b.tables.ntypes == 16 and int(b.tables.nref.max()) == 7
+    d3 = handle(b.tables, precision)
+    pos, typ = to_dev(b)
+    out = d3.compute_batch(pos, typ, b.offsets, b.cells, b.pbc)
+    d3.sync_status()
+    (assert_fp64_ok if precision == "fp64" else assert_mixed_ok)(out, oracle_mod.compute_batch(b, PRM), b.offsets)
+
+
+def test_table_limits_backward(torch_cuda):
+    """Mixed and FP64 backward agree at the table limits (16 types, 7 references)."""
+    torch = torch_cuda
+    b = _limit_batch()
+    pos, typ = to_dev(b)
+    g = torch.Generator(device="cuda").manual_seed(3)
+    gE = torch.randn(b.nstruct, dtype=torch.float64, device="cuda", generator=g)
+    gF = 0.01 * torch.randn(b.natoms, 3, dtype=torch.float64, device="cuda", generator=g)
+    res = {}
+    for prec in ("fp64", "mixed"):
+        d3 = handle(b.tables, prec)
+        r = d3.backward(pos, typ, b.offsets, b.cells, b.pbc, gE, gF)
+        d3.sync_status()
+        res[prec] = {k: v.cpu().numpy() for k, v in r.items()}
+    m, f = res["mixed"], res["fp64"]
+    assert np.all(np.abs(m["dparams"] - f["dparams"]) <= 1e-6 * np.abs(f["dparams"]))
+    assert np.abs(m["dpos"] - f["dpos"]).max() <= 1e-6 * np.abs(f["dpos"]).max()

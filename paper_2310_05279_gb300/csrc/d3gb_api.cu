@@ -348,7 +348,18 @@ d3_status plan_alloc(d3_handle* h, Plan& P) {
     int64_t maxn = 0;
     for (int s = 0; s < B; ++s) maxn = std::max<int64_t>(maxn, P.geo[s].natoms);
     w.max_natoms = maxn;
-    A(w.fin_part, double, 7 * (int64_t)B * std::max<int64_t>(1, (maxn + 4095) / 4096));
+    std::vector<int> fin_sid;
+    int64_t nfin = 0;
+    for (int s = 0; s < B; ++s) {
+        P.geo[s].fin_base = nfin;
+        const int64_t k = (P.geo[s].natoms + kFinChunk - 1) / kFinChunk;
+        nfin += k;
+        fin_sid.insert(fin_sid.end(), (size_t)k, s);
+    }
+    w.n_fin = nfin;
+    A(w.fin_part, double, 7 * std::max<int64_t>(1, nfin));
+    int* dfin = nullptr;
+    A(dfin, int, std::max<int64_t>(1, nfin));
     A(P.bsum, int, scan_scratch_ints(C));
 #undef A
     if (e != cudaSuccess) {
@@ -360,6 +371,7 @@ d3_status plan_alloc(d3_handle* h, Plan& P) {
     P.w.geo = dgeo;
     P.w.offsets = doff;
     P.w.sid_in = dsid;
+    P.w.fin_sid = dfin;
     const double rld = list_radius(h, h->prm.rc_disp_A), rln = list_radius(h, h->prm.rc_cn_A);
     w.rl_disp2 = (float)(rld * rld);
     w.rl_cn2 = (float)(rln * rln);
@@ -370,6 +382,8 @@ d3_status plan_alloc(d3_handle* h, Plan& P) {
     w.gate = nullptr;  // the plan's own Work builds unconditionally; enqueue_build gates a copy
     P.gate = gate;
     e = cudaMemcpy(dgeo, P.geo.data(), sizeof(StructGeo) * B, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && nfin > 0)
+        e = cudaMemcpy(dfin, fin_sid.data(), sizeof(int) * (size_t)nfin, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(doff, P.offsets.data(), sizeof(int64_t) * (B + 1), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && Nr > 0) {
         std::vector<int> sid((size_t)Nr);

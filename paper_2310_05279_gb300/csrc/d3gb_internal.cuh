@@ -33,6 +33,7 @@ constexpr double kHartreeEV = 27.211386245988;  // eV per Hartree
 constexpr int kMaxTypes = 16;
 constexpr int kMaxRef = 7;
 constexpr int kChunk = 64;  // pairs summed in FP32 before an FP64 accumulate (mixed form)
+constexpr int kFinChunk = 4096;  // atoms per first-level block of the per-structure sums
 
 enum StatusBits : int {
     ST_GHOST_CAP = 1,
@@ -57,6 +58,7 @@ struct StructGeo {
     int32_t natoms;
     int32_t cap_disp, cap_cn;
     int32_t pad;
+    int64_t fin_base;   // first chunk of the structure in the per-structure sums
     int64_t list_base_disp, list_base_cn;
 };
 
@@ -120,7 +122,9 @@ struct Work {
     double* eat;             // [Nr] site energies, Ha
     double* wv;              // [Nr][6] per-atom virial (xx yy zz xy xz yz), Ha
     void* Pv;                // [Nr][4] real: P_i = sum_j (dU_j/dn_i) r_ij (per-atom virial of Eq. 7 only)
-    double* fin_part;        // [B][ceil(max_natoms / 4096)][7] chunk sums
+    double* fin_part;        // [n_fin][7] chunk sums, structure s owning chunks [fin_base_s, fin_base_s + ceil(natoms_s / kFinChunk))
+    const int* fin_sid;      // [n_fin] structure of each chunk
+    int64_t n_fin;           // chunks over the batch
     int64_t max_natoms;
     int* status;
 };

@@ -639,14 +639,15 @@ __global__ void __launch_bounds__(128) k_chain(Work w, Consts c, const float4* _
 
 // ------------------------------------------------------------------ per-structure sums
 // Two fixed-order levels: block (s, c) sums atoms [c*kFinChunk, (c+1)*kFinChunk)
-// of structure s into part[s][c][7]; one block per structure then adds its
-// chunks in order.  Deterministic for any batch shape.
-constexpr int kFinChunk = 4096;
-
-__global__ void __launch_bounds__(256) k_fin_chunks(Work w, double* __restrict__ part, int nchunk) {
-    const int s = blockIdx.x, ch = blockIdx.y;
+// of structure s into part[fin_base_s + c][7]; then warp s adds its structure's
+// chunk sums (a strided pass and a shuffle tree, both in a fixed order).
+// Deterministic for any batch shape.
+__global__ void __launch_bounds__(256) k_fin_chunks(Work w, double* __restrict__ part) {
+    const int64_t cid = blockIdx.x;
+    const int s = w.fin_sid[cid];
     const StructGeo& G = w.geo[s];
-    const int64_t k0 = (int64_t)ch * kFinChunk, k1 = k0 + kFinChunk < (int64_t)G.natoms ? k0 + kFinChunk : (int64_t)G.natoms;
+    const int64_t k0 = (cid - G.fin_base) * kFinChunk;
+    const int64_t k1 = k0 + kFinChunk < (int64_t)G.natoms ? k0 + kFinChunk : (int64_t)G.natoms;
     double acc[7] = {0, 0, 0, 0, 0, 0, 0};
     for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
         const int64_t p = G.atom_base + k;
@@ -664,18 +665,25 @@ __global__ void __launch_bounds__(256) k_fin_chunks(Work w, double* __restrict__
             for (int m = 0; m < 7; ++m) red[m][threadIdx.x] += red[m][threadIdx.x + o];
         __syncthreads();
     }
-    if (threadIdx.x < 7) part[((int64_t)s * nchunk + ch) * 7 + threadIdx.x] = red[threadIdx.x][0];
+    if (threadIdx.x < 7) part[cid * 7 + threadIdx.x] = red[threadIdx.x][0];
 }
 
-__global__ void k_fin_struct(Work w, const double* __restrict__ part, int nchunk, double* __restrict__ E,
-                             double* __restrict__ Wout, int accumulate) {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= w.B) return;
-    const int nc = (w.geo[s].natoms + kFinChunk - 1) / kFinChunk;
+__global__ void __launch_bounds__(128) k_fin_struct(Work w, const double* __restrict__ part,
+                                                    double* __restrict__ E, double* __restrict__ Wout,
+                                                    int accumulate) {
+    const int s = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (s >= w.B) return;  // whole warps leave together
+    const StructGeo& G = w.geo[s];
+    const int nc = (int)((G.natoms + kFinChunk - 1) / kFinChunk);
     double acc[7] = {0, 0, 0, 0, 0, 0, 0};
-    for (int ch = 0; ch < nc; ++ch)
+    for (int ch = lane; ch < nc; ch += 32)
 #pragma unroll
-        for (int m = 0; m < 7; ++m) acc[m] += part[((int64_t)s * nchunk + ch) * 7 + m];
+        for (int m = 0; m < 7; ++m) acc[m] += part[(G.fin_base + ch) * 7 + m];
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int m = 0; m < 7; ++m) acc[m] += __shfl_xor_sync(0xffffffffu, acc[m], o);
+    if (lane != 0) return;
     const double h = kHartreeEV;
     const double v[9] = {acc[1] * h, acc[4] * h, acc[5] * h, acc[4] * h, acc[2] * h, acc[6] * h,
                          acc[5] * h, acc[6] * h, acc[3] * h};
@@ -723,9 +731,8 @@ cudaError_t forward_impl(const Work& w, const Consts& c, const Tabs& tb, double*
     }
     mark(4);
     if (B > 0) {
-        const int nchunk = (int)((w.max_natoms + kFinChunk - 1) / kFinChunk);
-        if (nchunk > 0) k_fin_chunks<<<dim3(B, nchunk), 256, 0, st>>>(w, w.fin_part, nchunk);
-        k_fin_struct<<<nblk(B, 128), 128, 0, st>>>(w, w.fin_part, nchunk > 0 ? nchunk : 1, E, W, c.accumulate);
+        if (w.n_fin > 0) k_fin_chunks<<<(unsigned)w.n_fin, 256, 0, st>>>(w, w.fin_part);
+        k_fin_struct<<<nblk((int64_t)B * 32, 128), 128, 0, st>>>(w, w.fin_part, E, W, c.accumulate);
     }
     mark(5);
     return cudaGetLastError();

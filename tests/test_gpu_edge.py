@@ -60,6 +60,30 @@ def test_empty_structures_and_small_cells(torch_cuda, oracle_mod, precision):
     assert out["E"][0].item() == 0.0 and out["E"][3].item() == 0.0
 
 
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_per_structure_sums_ragged(torch_cuda, oracle_mod, precision):
+    """Per-structure E and W when structures span several first-level sum blocks
+    (4096 atoms each) next to one-block and empty structures."""
+    names = ["H", "C", "O"]
+    tabs = wl.random_tables(names, 6)
+    g = np.random.Generator(np.random.PCG64(12))
+    sizes = [9000, 37, 0, 4096, 4097, 300]
+    structs = [wl.random_structure(g, n, names) if n > 0 else
+               (np.zeros((0, 3)), np.zeros(0, np.int32), np.eye(3) * 8.0, np.ones(3, np.int32)) for n in sizes]
+    b = wl.batch_of(structs, tabs)
+    d3 = handle(tabs, precision)
+    pos, typ = to_dev(b)
+    out = d3.compute_batch(pos, typ, b.offsets, b.cells, b.pbc, e_atom=True)
+    d3.sync_status()
+    ref = oracle_mod.compute_batch(b, PRM)
+    (assert_fp64_ok if precision == "fp64" else assert_mixed_ok)(out, ref, b.offsets)
+    ea = out["e_atom"].cpu().numpy()
+    E = out["E"].cpu().numpy()
+    for s in range(len(sizes)):
+        part = ea[b.offsets[s]:b.offsets[s + 1]].sum()
+        assert abs(part - E[s]) <= 1e-9 * max(abs(E[s]), 1e-30)
+
+
 def test_open_atoms_outside_cell(torch_cuda, oracle_mod):
     """Open boundaries with atoms far outside the given cell (clamped into edge bins)."""
     tabs = wl.carbon_table()

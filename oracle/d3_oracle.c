@@ -33,6 +33,8 @@
  *      many-body, Sec. II A after Eq. 4).
  *   6. Virial W = -sum over instances d (x) dE/dd, the sum of the per-atom
  *      virials of Eq. 7.
+ *   7. Optionally (s9 != 0), the three-body term of the original D3 model, which
+ *      the paper excludes; see atm_triangle.
  *
  * Units: positions and cells in Angstrom; a2, Rcov, sqrt(Q) in bohr; C6ref in
  * Ha*bohr^6; all formulae evaluated in bohr/Hartree; E in eV, F in eV/A, W in eV.
@@ -57,6 +59,7 @@ typedef struct {
     double s6, s8, a1, a2_bohr; /* BJ damping of Eq. 2 */
     double k1, k2, k3;          /* Eq. 4 steepness, covalent-radius scale, Eq. 3 Gaussian width */
     double rc_disp_A, rc_cn_A;  /* R_pot and R_cn */
+    double s9, alpha9, rc3_A;   /* optional three-body term (s9 = 0: off), see atm_triangle */
 } oracle_params;
 
 typedef struct {
@@ -127,6 +130,85 @@ static void ref_weights(const oracle_tables *t, int ti, double n, double k3, dou
     double gbar = 0.0;
     for (int a = 0; a < nr; ++a) gbar += W[a] * (-2.0 * k3 * (n - t->cn_ref[ti * R + a]));
     for (int a = 0; a < nr; ++a) dW[a] = W[a] * (-2.0 * k3 * (n - t->cn_ref[ti * R + a]) - gbar);
+}
+
+/* C6 of one pair from the per-atom weights (Eq. 3) and its derivatives with
+ * respect to the two atoms' coordination numbers. */
+static double pair_c6(const oracle_tables *t, const double *Wt, const double *dWt, int64_t i, int ti, int64_t j,
+                      int tj, double *dCi, double *dCj) {
+    int R = t->max_ref;
+    const double *cref = t->c6_ref + ((size_t)(ti * t->ntypes + tj) * R) * R;
+    double C6 = 0.0, di = 0.0, dj = 0.0;
+    for (int a = 0; a < R; ++a)
+        for (int b = 0; b < R; ++b) {
+            double c = cref[a * R + b];
+            C6 += Wt[R * i + a] * Wt[R * j + b] * c;
+            di += dWt[R * i + a] * Wt[R * j + b] * c;
+            dj += Wt[R * i + a] * dWt[R * j + b] * c;
+        }
+    *dCi = di;
+    *dCj = dj;
+    return C6;
+}
+
+/* Damping radius R = a1 R0 + a2 of Eq. 2 for a type pair, and R0. */
+static double damp_radius(const oracle_params *p, const oracle_tables *t, int ti, int tj, double *R0) {
+    *R0 = sqrt(3.0 * t->sqrtq[ti] * t->sqrtq[tj]);
+    return p->a1 * *R0 + p->a2_bohr;
+}
+
+/*
+ * Optional three-body (Axilrod-Teller-Muto triple-dipole) term of the original
+ * D3 model (Grimme et al., J. Chem. Phys. 132, 154104 (2010)).  The paper leaves
+ * it out (Sec. II A); it is evaluated only when s9 != 0.  For a triangle of atoms
+ * i, j, k with sides u = r_ij, v = r_ik, w = r_jk and interior angles A_i, A_j, A_k:
+ *
+ *   E = s9 sqrt(C6_ij C6_ik C6_jk) (3 cos A_i cos A_j cos A_k + 1) / (u v w)^3 * f,
+ *   f = 1 / (1 + 6 q),   q = (Rbar / rbar)^alpha9,
+ *
+ * rbar = (u v w)^(1/3) and Rbar the geometric mean of the three damping radii
+ * R = a1 R0 + a2 of Eq. 2 (the Becke-Johnson radii in the zero-damping form of
+ * the three-body damping).  The cosines come from the law of cosines.
+ *
+ * Outputs the energy, dE/du, dE/dv, dE/dw, dE/dR for the three radii (in the
+ * order ij, ik, jk; for the a1/a2 derivatives) given the three C6 values.
+ */
+static double atm_triangle(const oracle_params *p, double u, double v, double w, double C6ij, double C6ik,
+                           double C6jk, double Rij, double Rik, double Rjk, double *dEdu, double *dEdv,
+                           double *dEdw, double dEdR[3]) {
+    double ci = (u * u + v * v - w * w) / (2.0 * u * v);
+    double cj = (u * u + w * w - v * v) / (2.0 * u * w);
+    double ck = (v * v + w * w - u * u) / (2.0 * v * w);
+    /* partial derivatives of each cosine with respect to each side */
+    double ci_u = 1.0 / (2.0 * v) - v / (2.0 * u * u) + w * w / (2.0 * u * u * v);
+    double ci_v = 1.0 / (2.0 * u) - u / (2.0 * v * v) + w * w / (2.0 * u * v * v);
+    double ci_w = -w / (u * v);
+    double cj_u = 1.0 / (2.0 * w) - w / (2.0 * u * u) + v * v / (2.0 * u * u * w);
+    double cj_w = 1.0 / (2.0 * u) - u / (2.0 * w * w) + v * v / (2.0 * u * w * w);
+    double cj_v = -v / (u * w);
+    double ck_v = 1.0 / (2.0 * w) - w / (2.0 * v * v) + u * u / (2.0 * v * v * w);
+    double ck_w = 1.0 / (2.0 * v) - v / (2.0 * w * w) + u * u / (2.0 * v * w * w);
+    double ck_u = -u / (v * w);
+    double prod = u * v * w;
+    double inv3 = 1.0 / (prod * prod * prod);
+    double ang = 3.0 * ci * cj * ck + 1.0;
+    double G = ang * inv3;
+    double G_u = 3.0 * (ci_u * cj * ck + ci * cj_u * ck + ci * cj * ck_u) * inv3 - 3.0 * G / u;
+    double G_v = 3.0 * (ci_v * cj * ck + ci * cj_v * ck + ci * cj * ck_v) * inv3 - 3.0 * G / v;
+    double G_w = 3.0 * (ci_w * cj * ck + ci * cj_w * ck + ci * cj * ck_w) * inv3 - 3.0 * G / w;
+    double Rbar = cbrt(Rij * Rik * Rjk), rbar = cbrt(prod);
+    double q = pow(Rbar / rbar, p->alpha9);
+    double f = 1.0 / (1.0 + 6.0 * q);
+    /* dq/du = -(alpha/3) q / u, so df/du = 2 alpha q f^2 / u; dq/dR = (alpha/3) q / R */
+    double fs = 2.0 * p->alpha9 * q * f * f;
+    double c = p->s9 * sqrt(C6ij * C6ik * C6jk);
+    *dEdu = c * (G_u * f + G * fs / u);
+    *dEdv = c * (G_v * f + G * fs / v);
+    *dEdw = c * (G_w * f + G * fs / w);
+    dEdR[0] = -c * G * fs / Rij;
+    dEdR[1] = -c * G * fs / Rik;
+    dEdR[2] = -c * G * fs / Rjk;
+    return c * G * f;
 }
 
 /* ------------------------------------------------------------------ instance search */
@@ -210,7 +292,10 @@ int d3_oracle_compute(const oracle_params *p, const oracle_tables *t, int64_t n,
         if (types[i] < 0 || types[i] >= t->ntypes) return -2;
     const int R = t->max_ref;
     const double rcd = p->rc_disp_A / ORACLE_BOHR_A, rcn = p->rc_cn_A / ORACLE_BOHR_A;
-    const double rmax = rcd > rcn ? rcd : rcn;
+    const int atm = p->s9 != 0.0;
+    const double rc3 = atm ? p->rc3_A / ORACLE_BOHR_A : 0.0;
+    double rmax = rcd > rcn ? rcd : rcn;
+    if (rc3 > rmax) rmax = rc3;
 
     /* lattice in bohr, wrapped positions in bohr */
     double Hb[9], Hi[9];
@@ -301,6 +386,63 @@ int d3_oracle_compute(const oracle_params *p, const oracle_tables *t, int64_t n,
         dp[2] += de_dR * R0;
         dp[3] += de_dR;
     }
+    /* optional three-body term: every triangle whose three sides are below rc3.
+     * Atom i's instances are contiguous in I; each unordered pair of them (j, k)
+     * with |d_k - d_j| < rc3 is one triangle seen from vertex i.  Every triangle
+     * is seen once from each of its three vertices, so each sighting carries a
+     * third of the energy and of every derivative, the derivatives taken with
+     * respect to all three atoms. */
+    if (atm) {
+        int64_t *start = (int64_t *)calloc((size_t)(n + 1), sizeof(int64_t));
+        for (int64_t q = 0; q < ni; ++q) start[I[q].i + 1]++;
+        for (int64_t i = 0; i < n; ++i) start[i + 1] += start[i];
+        const double third = 1.0 / 3.0;
+        for (int64_t i = 0; i < n; ++i) {
+            for (int64_t qa = start[i]; qa < start[i + 1]; ++qa) {
+                const instance *A = &I[qa];
+                if (!(A->r < rc3)) continue;
+                for (int64_t qb = qa + 1; qb < start[i + 1]; ++qb) {
+                    const instance *Bq = &I[qb];
+                    if (!(Bq->r < rc3)) continue;
+                    double djk[3] = {Bq->d[0] - A->d[0], Bq->d[1] - A->d[1], Bq->d[2] - A->d[2]};
+                    double w = sqrt(djk[0] * djk[0] + djk[1] * djk[1] + djk[2] * djk[2]);
+                    if (!(w < rc3)) continue;
+                    int64_t j = A->j, k = Bq->j;
+                    int ti = types[i], tj = types[j], tk = types[k];
+                    double dij_i, dij_j, dik_i, dik_k, djk_j, djk_k;
+                    double C6ij = pair_c6(t, Wt, dWt, i, ti, j, tj, &dij_i, &dij_j);
+                    double C6ik = pair_c6(t, Wt, dWt, i, ti, k, tk, &dik_i, &dik_k);
+                    double C6jk = pair_c6(t, Wt, dWt, j, tj, k, tk, &djk_j, &djk_k);
+                    double R0ij, R0ik, R0jk;
+                    double Rij = damp_radius(p, t, ti, tj, &R0ij), Rik = damp_radius(p, t, ti, tk, &R0ik),
+                           Rjk = damp_radius(p, t, tj, tk, &R0jk);
+                    double Eu, Ev, Ew, ER[3];
+                    double e = atm_triangle(p, A->r, Bq->r, w, C6ij, C6ik, C6jk, Rij, Rik, Rjk, &Eu, &Ev, &Ew, ER);
+                    Etot += third * e;
+                    eat[i] += third * e;
+                    /* dE/dC6 = E / (2 C6) for each of the three pairs */
+                    dEdn[i] += third * 0.5 * e * (dij_i / C6ij + dik_i / C6ik);
+                    dEdn[j] += third * 0.5 * e * (dij_j / C6ij + djk_j / C6jk);
+                    dEdn[k] += third * 0.5 * e * (dik_k / C6ik + djk_k / C6jk);
+                    /* edge vectors d and dE/dd: ij = A->d, ik = Bq->d, jk = djk */
+                    const double *dv[3] = {A->d, Bq->d, djk};
+                    const double len[3] = {A->r, Bq->r, w}, dl[3] = {Eu, Ev, Ew};
+                    const int64_t from[3] = {i, i, j}, to[3] = {j, k, k};
+                    for (int ed = 0; ed < 3; ++ed)
+                        for (int a = 0; a < 3; ++a) {
+                            double g = third * dl[ed] * dv[ed][a] / len[ed];
+                            Fb[3 * from[ed] + a] += g;
+                            Fb[3 * to[ed] + a] -= g;
+                            for (int b = 0; b < 3; ++b) Wv[3 * a + b] -= dv[ed][a] * third * dl[ed] * dv[ed][b] / len[ed];
+                        }
+                    /* dR/da1 = R0, dR/da2 = 1 */
+                    dp[2] += third * (ER[0] * R0ij + ER[1] * R0ik + ER[2] * R0jk);
+                    dp[3] += third * (ER[0] + ER[1] + ER[2]);
+                }
+            }
+        }
+        free(start);
+    }
     /* chain rule through the coordination numbers (Eq. 4 inside Eq. 3) */
     for (int64_t q = 0; q < ni; ++q) {
         const instance *s = &I[q];
@@ -355,6 +497,7 @@ int d3_oracle_compute(const oracle_params *p, const oracle_tables *t, int64_t n,
 int d3_oracle_atom_virial(const oracle_params *p, const oracle_tables *t, int64_t n, const double *pos,
                           const int32_t *types, const double *cell, const int32_t *pbc, double *w_atom) {
     if (n < 0 || !p || !t || !w_atom) return -1;
+    if (p->s9 != 0.0) return -4; /* Eq. 7 is defined for the two-body site energies only */
     for (int64_t i = 0; i < n; ++i)
         if (types[i] < 0 || types[i] >= t->ntypes) return -2;
     const int R = t->max_ref;

@@ -5,7 +5,8 @@
 structures of a batch in order.  Inputs are numpy arrays in Angstrom; outputs
 are E (eV), F (eV/A), W (eV, 3x3), the site energies U_i (eV), the
 coordination numbers n_i, dE/dn_i (eV) and dE/d(s6, s8, a1, a2) (eV);
-``atom_virial()`` gives the per-atom virials of Eq. 7.
+``atom_virial()`` gives the per-atom virials of Eq. 7.  A nonzero ``s9`` in the
+parameters adds the optional three-body term (see ``atm_triangle`` in the C source).
 """
 from __future__ import annotations
 
@@ -37,7 +38,8 @@ def build(force: bool = False) -> str:
 
 
 class _Params(C.Structure):
-    _fields_ = [(k, C.c_double) for k in ("s6", "s8", "a1", "a2_bohr", "k1", "k2", "k3", "rc_disp_A", "rc_cn_A")]
+    _fields_ = [(k, C.c_double) for k in ("s6", "s8", "a1", "a2_bohr", "k1", "k2", "k3", "rc_disp_A", "rc_cn_A",
+                                          "s9", "alpha9", "rc3_A")]
 
 
 class _Tables(C.Structure):
@@ -70,10 +72,18 @@ def num_threads() -> int:
 
 
 def params_from(p: dict) -> dict:
-    """Normalise a parameter dict (keys s6, s8, a1, a2 [bohr], k1, k2, k3, rc_disp, rc_cn [A])."""
+    """Normalise a parameter dict (keys s6, s8, a1, a2 [bohr], k1, k2, k3, rc_disp, rc_cn [A]; optional
+    three-body term: s9 (0 = off), alpha9, rc3 [A], default rc_cn)."""
+    rc_cn = float(p.get("rc_cn", 6.0))
     return dict(s6=float(p["s6"]), s8=float(p["s8"]), a1=float(p["a1"]), a2=float(p["a2"]),
                 k1=float(p.get("k1", 16.0)), k2=float(p.get("k2", 4.0 / 3.0)), k3=float(p.get("k3", 4.0)),
-                rc_disp=float(p.get("rc_disp", 12.0)), rc_cn=float(p.get("rc_cn", 6.0)))
+                rc_disp=float(p.get("rc_disp", 12.0)), rc_cn=rc_cn, s9=float(p.get("s9", 0.0)),
+                alpha9=float(p.get("alpha9", 16.0)), rc3=float(p.get("rc3", rc_cn)))
+
+
+def _cparams(p: dict) -> _Params:
+    return _Params(p["s6"], p["s8"], p["a1"], p["a2"], p["k1"], p["k2"], p["k3"], p["rc_disp"], p["rc_cn"],
+                   p["s9"], p["alpha9"], p["rc3"])
 
 
 def _ptr(a, ct):
@@ -96,7 +106,7 @@ def compute(pos, types, cell, pbc, tables, params: dict) -> dict:
     """Evaluate one structure; returns a dict of numpy results."""
     lib = _load()
     p = params_from(params)
-    P = _Params(p["s6"], p["s8"], p["a1"], p["a2"], p["k1"], p["k2"], p["k3"], p["rc_disp"], p["rc_cn"])
+    P = _cparams(p)
     th = _TableHold(tables)
     pos = np.ascontiguousarray(pos, np.float64).reshape(-1, 3)
     types = np.ascontiguousarray(types, np.int32).reshape(-1)
@@ -124,7 +134,7 @@ def atom_virial(pos, types, cell, pbc, tables, params: dict) -> np.ndarray:
     (W_i[a, b] = sum_j (r_ij)_a (dU_j/dr_ji)_b)."""
     lib = _load()
     p = params_from(params)
-    P = _Params(p["s6"], p["s8"], p["a1"], p["a2"], p["k1"], p["k2"], p["k3"], p["rc_disp"], p["rc_cn"])
+    P = _cparams(p)
     th = _TableHold(tables)
     pos = np.ascontiguousarray(pos, np.float64).reshape(-1, 3)
     types = np.ascontiguousarray(types, np.int32).reshape(-1)

@@ -45,6 +45,17 @@ def disp_flops_per_pair(nref: int) -> int:
     return 53 + 6 * nref
 
 
+# FP32 work of one evaluation of the optional three-body term per unique triangle
+# (FMA = 2 FLOP): three side vectors and squared lengths 24 + the C6 of the third
+# pair 2*Nref + P, P^(-1/2), P^(-3/2) 9 + the law-of-cosines factors and N 8 +
+# angular factor 4 + damping q, f and x df/dx 16 + sqrt(C6 C6 C6) and s9 8 +
+# energy 2 + dN/dx for three sides 14 + dE/d(side^2) for three sides 36 + dE/dn for
+# three atoms 8 + forces on three atoms 18 + symmetric virial of three sides 36
+# = 183 + 2*Nref.  (The kernel evaluates each triangle from all three vertices.)
+def atm_flops_per_triangle(nref: int) -> int:
+    return 183 + 2 * nref
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -205,6 +216,22 @@ def count_pairs(torch, batch, rc, dev):
     return tot
 
 
+def count_triangles(torch, batch, rc, dev):
+    """Unique triangles with all three sides below rc over the batch: trace(A^3)/6 of
+    each structure's adjacency matrix (minimum image is exact, as in count_pairs)."""
+    tot = 0
+    for s in range(batch.nstruct):
+        pos, _, cell, _ = batch.structure(s)
+        L = torch.tensor(np.diag(cell), dtype=torch.float64, device=dev)
+        x = torch.tensor(pos, dtype=torch.float64, device=dev)
+        d = x[:, None, :] - x[None, :, :]
+        d = d - L * torch.round(d / L)
+        r2 = (d * d).sum(-1)
+        A = ((r2 < rc * rc) & (r2 > 0)).to(torch.float32)
+        tot += int(round(float(((A @ A) * A).sum().item()))) // 6
+    return tot
+
+
 def cpu_baseline(batch, params, budget_s=15.0):
     """The FP64 oracle, as it stands, on a bounded sample of the workload's structures."""
     import oracle
@@ -273,6 +300,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--no-graphs", action="store_true", help="enqueue every kernel directly (no graph replay)")
+    ap.add_argument("--three-body-steps", type=int, default=5,
+                    help="steps of the extra leg with the optional three-body term (0: skip)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -360,6 +389,32 @@ def main():
                 "stage_ms": {k: proff["ms"][k] / max(1, proff["calls"][k]) for k in proff["ms"]},
                 "mixed_speedup": msf / ms}
 
+    # the optional three-body term (not part of the paper's model) on the same batch:
+    # the whole step with it on, and its own pass against the FP32 roofline
+    three_body = None
+    if args.three_body_steps > 0:
+        atm = dict(s9=1.0, alpha9=16.0, rc3=params["rc_cn"])
+        d3a = D3(batch.tables, dict(params, **atm), precision="mixed")
+        outa = d3a.compute_batch(pos, typ, batch.offsets, batch.cells, batch.pbc)
+        d3a.sync_status()
+
+        def step_atm():
+            d3a.compute_batch(pos, typ, batch.offsets, batch.cells, batch.pbc, out=outa)
+        ta = time_steps(torch, step_atm, args.three_body_steps, 3, flush=flush, stream=stream)
+        d3a.profile(True)
+        time_steps(torch, step_atm, args.three_body_steps, 1, flush=flush, stream=stream)
+        profa = d3a.profile_read()
+        d3a.profile(False)
+        d3a.sync_status()
+        del d3a
+        msa = reduce_max(sum(ta) / len(ta), dev)
+        stage_a = {k: profa["ms"][k] / max(1, profa["calls"][k]) for k in profa["ms"]}
+        tri = count_triangles(torch, batch, atm["rc3"], dev)
+        three_body = {"value": job_value(N, world, msa * 1e-3), "unit": UNIT, "ms_per_step": msa,
+                      "three_body_ms": stage_a["three_body"], "stage_ms": stage_a, "triangles": tri,
+                      "params": atm, "note": "optional triple-dipole term; the paper's model leaves it out",
+                      "flop_per_triangle": None}
+
     # end to end through the host-memory entry point (pinned buffers, copies inside)
     e2e = None
     if not args.no_e2e:
@@ -399,6 +454,14 @@ def main():
             "algorithmic": f"{disp_flops_per_pair(nref)} FLOP per unique pair within 12 A x {pairs:.4g} pairs",
             "timing": "k_disp stage events over the same number of steps, kernels enqueued directly"}
 
+    if three_body is not None:
+        fl = atm_flops_per_triangle(nref)
+        tf = fl * three_body["triangles"] / (three_body["three_body_ms"] * 1e-3) / 1e12
+        three_body["flop_per_triangle"] = fl
+        three_body["roofline"] = {"bound": "alu", "kernel": "k_atm", "achieved": tf, "peak": fp32_peak,
+                                  "unit": "TFLOP/s", "frac": tf / fp32_peak,
+                                  "algorithmic": f"{fl} FLOP per unique triangle x {three_body['triangles']:.4g}"}
+
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -412,6 +475,7 @@ def main():
             "roofline": roof,
             "stage_ms": stage_ms, "dominant_stage": dom,
             "fp64_form": fp64,
+            "three_body": three_body,
             "e2e": e2e,
             "gpu_launches": int(round(launches_per_step * args.steps)),
             "gpu_launches_per_step": launches_per_step,

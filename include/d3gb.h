@@ -120,6 +120,26 @@ d3_status d3_set_graphs(d3_handle *h, int32_t on);
  * always overwritten.  Default off.  Applies to work enqueued afterwards. */
 d3_status d3_set_accumulate(d3_handle *h, int32_t on);
 
+/* Optional three-body term (off by default).  The paper's model is two-body:
+ * Sec. II A leaves out the triple-dipole term of the original D3 model, and so
+ * does every other entry point unless this one enables it.  With s9 != 0 the
+ * compute calls add, for every triangle (i, j, k) whose three sides are below
+ * rc3,
+ *   E_ijk = s9 sqrt(C6_ij C6_ik C6_jk) (3 cos A_i cos A_j cos A_k + 1)
+ *           / (r_ij r_ik r_jk)^3 / (1 + 6 (Rbar / rbar)^alpha9),
+ * A_v the interior angles, rbar = (r_ij r_ik r_jk)^(1/3) and Rbar the geometric
+ * mean of the three damping radii a1 R0 + a2 of Eq. 2 (bohr), with the
+ * C6 of Eq. 3 (so the term also acts through the coordination numbers), to E,
+ * F, W and the site energies (a third of E_ijk to each vertex).
+ *  s9      strength (0 turns the term off; 1 is the usual D3 value)
+ *  alpha9  damping exponent, 0 < alpha9 <= 64 (16 in the original model)
+ *  rc3_A   cutoff on every side, 0 < rc3_A <= rc_cn_A, A (the triangles are
+ *          taken from the CN neighbour lists)
+ * With the term on, d3_compute_batch_atoms and d3_backward return D3_ERR_ARG
+ * (per-atom virials and the gradients are those of the two-body model).
+ * Synchronises with the handle's last stream; applies to work enqueued afterwards. */
+d3_status d3_set_three_body(d3_handle *h, double s9, double alpha9, double rc3_A);
+
 /* Build (or rebuild) the neighbour lists of a batch and size the workspace
  * for it; synchronises.  The cell-list build: wrap into the cell, periodic
  * image atoms within the list radius, counting sort by cell, and per-atom
@@ -210,14 +230,18 @@ const char *d3_last_error(const d3_handle *h);
 /* Stage timing for benchmarks and profiling.  While enabled, every later
  * compute call brackets its stages with CUDA events on the call's stream:
  * 0 neighbour build, 1 coordination numbers (Eq. 4), 2 reference weights
- * (Eq. 3), 3 dispersion pass (Eq. 2), 4 coordination-number chain rule,
- * 5 per-structure sums.  Events are cheap stream markers; they add no
- * synchronisation.  The library also counts every kernel it launches. */
+ * (Eq. 3), 3 dispersion pass (Eq. 2), 4 three-body term (d3_set_three_body),
+ * 5 coordination-number chain rule, 6 per-structure sums.  Events are cheap
+ * stream markers; they add no synchronisation.  The library also counts every
+ * kernel it launches. */
 d3_status d3_profile_enable(d3_handle *h, int32_t on);
 
 /* Synchronise on the recorded events and return totals since the last reset:
- * ms[6] milliseconds per stage and calls[6] calls timed per stage (either may
- * be NULL); *launches = kernels launched by the library (may be NULL). */
+ * ms[7] milliseconds per stage and calls[7] calls timed per stage (either may
+ * be NULL); *launches = kernels launched by the library (may be NULL).  Stages:
+ * neighbour build, CN (Eq. 4, with the Eq. 3 weights), weights (empty: formed
+ * in the CN pass), dispersion (Eq. 2), three-body (empty unless enabled),
+ * CN chain rule, per-structure sums. */
 d3_status d3_profile_read(d3_handle *h, double *ms, int64_t *calls, int64_t *launches);
 
 /* Zero the stage totals and the launch counter. */

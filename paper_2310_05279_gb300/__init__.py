@@ -77,6 +77,8 @@ class D3:
         if st != 0:
             raise D3Error(st, "d3_create failed")
         self.h = h
+        if float(self.params.get("s9", 0.0)) != 0.0:  # optional three-body term
+            self.set_three_body(self.params["s9"], self.params.get("alpha9", 16.0), self.params.get("rc3"))
 
     def __del__(self):
         h = getattr(self, "h", None)
@@ -196,15 +198,15 @@ class D3:
         self._check(st)
         return dict(dparams=gp, dpos=gx)
 
-    STAGES = ("build", "cn", "weights", "disp", "chain", "finalize")
+    STAGES = ("build", "cn", "weights", "disp", "three_body", "chain", "finalize")
 
     def profile(self, on: bool = True):
         """Bracket every stage of later calls with CUDA events (see d3_profile_enable)."""
         self._check(self.lib.d3_profile_enable(self.h, 1 if on else 0))
 
     def profile_read(self) -> dict:
-        ms = (C.c_double * 6)()
-        calls = (C.c_int64 * 6)()
+        ms = (C.c_double * len(self.STAGES))()
+        calls = (C.c_int64 * len(self.STAGES))()
         launches = C.c_int64()
         self._check(self.lib.d3_profile_read(self.h, ms, calls, C.byref(launches)))
         return dict(ms={k: ms[i] for i, k in enumerate(self.STAGES)},
@@ -219,6 +221,13 @@ class D3:
     def set_graphs(self, on: bool = True):
         """Replay repeated compute calls as one CUDA graph (default on)."""
         self._check(self.lib.d3_set_graphs(self.h, 1 if on else 0))
+
+    def set_three_body(self, s9: float = 1.0, alpha9: float = 16.0, rc3: Optional[float] = None):
+        """Optional triple-dipole term that the paper leaves out (d3_set_three_body): s9 = 0 turns it
+        off; rc3 (A, default R_cn) bounds every side of a triangle and may not exceed R_cn."""
+        rc3 = float(self.params["rc_cn"]) if rc3 is None else float(rc3)
+        self._check(self.lib.d3_set_three_body(self.h, float(s9), float(alpha9), rc3))
+        self.params.update(s9=float(s9), alpha9=float(alpha9), rc3=rc3)
 
     def set_accumulate(self, on: bool = True):
         """Add E, F, W into the output tensors instead of overwriting them (Eq. 9 coupling)."""

@@ -47,6 +47,7 @@ SIGNATURES = {
     "d3_last_error": (C.c_char_p, [_vp]),
     "d3_build_count": (C.c_int, [_vp, _lp]),
     "d3_set_accumulate": (C.c_int, [_vp, C.c_int32]),
+    "d3_set_three_body": (C.c_int, [_vp, C.c_double, C.c_double, C.c_double]),
     "d3_set_graphs": (C.c_int, [_vp, C.c_int32]),
     "d3_version": (C.c_char_p, []),
     "d3_profile_enable": (C.c_int, [_vp, C.c_int32]),

@@ -34,6 +34,8 @@ using namespace d3gb;
 namespace {
 
 constexpr int kWindowCells = 3;  // list radius spans at most this many cells per axis
+// profiled stages: build, CN (with the Eq. 3 weights), weights, dispersion, three-body, chain, finalize
+constexpr int kStages = 7;
 
 struct DevBuf {
     std::vector<void*> ptrs;
@@ -83,6 +85,10 @@ struct d3_handle {
     float4* d_pairf = nullptr;
     dbl4* d_paird = nullptr;
     dbl4* d_pairb = nullptr;  // (R0, R, R0^2, 0) per element pair, for the backward
+    float* d_rtabf = nullptr;  // R = a1 R0 + a2 per element pair (three-body damping), both precisions
+    double* d_rtabd = nullptr;
+    // optional three-body term (d3_set_three_body); off while s9 == 0
+    double s9 = 0.0, alpha9 = 16.0, rc3_A = 0.0;
     float4* d_rcpair = nullptr;  // k2 (Rcov_i + Rcov_j) and its square, FP32 hi + lo
     float2* d_exptab = nullptr;  // 2^(j/64), j = 0..63, FP32 hi + lo
     double* d_rk = nullptr;
@@ -96,12 +102,12 @@ struct d3_handle {
     size_t stage_atoms = 0, stage_structs = 0;
     double *s_pos = nullptr, *s_E = nullptr, *s_F = nullptr, *s_W = nullptr;
     int32_t* s_types = nullptr;
-    // stage timing (d3_profile_*): 7 events per call, read back lazily
+    // stage timing (d3_profile_*): kStages + 1 events per call, read back lazily
     bool prof_on = false;
     std::vector<cudaEvent_t> ev_pool;
     std::vector<std::vector<cudaEvent_t>> ev_pending;
-    double prof_ms[6] = {0, 0, 0, 0, 0, 0};
-    int64_t prof_calls[6] = {0, 0, 0, 0, 0, 0};
+    double prof_ms[kStages] = {};
+    int64_t prof_calls[kStages] = {};
     int64_t launches = 0;
     bool accumulate = false;  // d3_set_accumulate
     // replay of the steady-state call as one CUDA graph (captured on cap_stream)
@@ -141,6 +147,8 @@ d3_status upload_pair_table(d3_handle* h) {
     const int T = h->T;
     std::vector<dbl4> pd(T * T), pb(T * T);
     std::vector<float4> pf(T * T);
+    std::vector<double> rd(T * T);
+    std::vector<float> rf(T * T);
     for (int a = 0; a < T; ++a)
         for (int b = 0; b < T; ++b) {
             const double R0sq = 3.0 * h->sqrtq[a] * h->sqrtq[b];
@@ -149,8 +157,12 @@ d3_status upload_pair_table(d3_handle* h) {
             pd[a * T + b] = dbl4_make(R6, R8, h->prm.s6, h->prm.s8 * R0sq);
             pf[a * T + b] = make_float4((float)R6, (float)R8, (float)h->prm.s6, (float)(h->prm.s8 * R0sq));
             pb[a * T + b] = dbl4_make(std::sqrt(R0sq), Rd, R0sq, 0.0);
+            rd[a * T + b] = Rd;
+            rf[a * T + b] = (float)Rd;
         }
     cudaError_t e = cudaMemcpy(h->d_paird, pd.data(), pd.size() * sizeof(dbl4), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(h->d_rtabd, rd.data(), rd.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(h->d_rtabf, rf.data(), rf.size() * sizeof(float), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(h->d_pairf, pf.data(), pf.size() * sizeof(float4), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(h->d_pairb, pb.data(), pb.size() * sizeof(dbl4), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(h, e, "pair table upload");
@@ -178,6 +190,11 @@ Consts make_consts(const d3_handle* h) {
     c.R = h->R;
     c.RP = h->RP;
     c.accumulate = h->accumulate ? 1 : 0;
+    c.atm = h->s9 != 0.0 ? 1 : 0;
+    c.s9 = h->s9;
+    c.alpha9 = h->alpha9;
+    const double r3 = h->rc3_A / kBohrA;
+    c.rc3_2 = r3 * r3;
     return c;
 }
 
@@ -508,6 +525,9 @@ d3_status forward(d3_handle* h, int32_t B, const int64_t* offsets, const double*
     if (s != D3_OK) return s;
     if (B > 0 && (!E || !W)) return fail(h, D3_ERR_ARG, "NULL E or W");
     if (offsets[B] > 0 && !F) return fail(h, D3_ERR_ARG, "NULL F");
+    if (w_atom && h->s9 != 0.0)
+        return fail(h, D3_ERR_ARG, "per-atom virials (Eq. 7) are defined for the two-body model only; "
+                                   "disable the three-body term");
     h->last_stream = st;
     if (B == 0) return D3_OK;
     s = ensure_plan(h, B, offsets, pos, types, cells, pbc, st);
@@ -515,8 +535,8 @@ d3_status forward(d3_handle* h, int32_t B, const int64_t* offsets, const double*
     Plan& P = h->plan;
     std::vector<cudaEvent_t> ev;
     if (h->prof_on) {
-        ev = take_events(h, 7);
-        if (ev.size() == 7) cudaEventRecord(ev[0], st);
+        ev = take_events(h, kStages + 1);
+        if (ev.size() == kStages + 1) cudaEventRecord(ev[0], st);
     }
     s = enqueue_build(h, P, pos, types, st, h->prm.skin_A > 0);
     if (s != D3_OK) return s;
@@ -529,11 +549,12 @@ d3_status forward(d3_handle* h, int32_t B, const int64_t* offsets, const double*
     tb.nref = h->d_nref;
     tb.rcpair = h->d_rcpair;
     tb.exptab = h->d_exptab;
+    tb.rtab = mixed ? (const void*)h->d_rtabf : (const void*)h->d_rtabd;
     cudaError_t e = launch_forward(P.w, c, mixed, tb, E, F, W, e_atom, cn, w_atom, B, st,
-                                   ev.size() == 7 ? ev.data() + 1 : nullptr);
+                                   ev.size() == kStages + 1 ? ev.data() + 1 : nullptr);
     if (e != cudaSuccess) return cuda_fail(h, e, "forward launch");
-    h->launches += (P.Nr > 0 ? kForwardLaunches : 1);
-    if (ev.size() == 7) h->ev_pending.push_back(ev);
+    h->launches += (P.Nr > 0 ? kForwardLaunches + c.atm : 1);
+    if (ev.size() == kStages + 1) h->ev_pending.push_back(ev);
     else for (cudaEvent_t x : ev) h->ev_pool.push_back(x);
     return D3_OK;
 }
@@ -663,6 +684,8 @@ d3_status d3_create(const d3_params* params, const d3_tables* tables, d3_handle*
     if (e == cudaSuccess) e = m.alloc(&h->d_pairf, T * T);
     if (e == cudaSuccess) e = m.alloc(&h->d_paird, T * T);
     if (e == cudaSuccess) e = m.alloc(&h->d_pairb, T * T);
+    if (e == cudaSuccess) e = m.alloc(&h->d_rtabf, T * T);
+    if (e == cudaSuccess) e = m.alloc(&h->d_rtabd, T * T);
     if (e == cudaSuccess) e = m.alloc(&h->d_rcpair, T * T);
     if (e == cudaSuccess) e = m.alloc(&h->d_exptab, 64);
     if (e == cudaSuccess) e = m.alloc(&h->d_rk, T);
@@ -731,6 +754,22 @@ d3_status d3_set_damping(d3_handle* h, double s6, double s8, double a1, double a
     h->prm.a2_bohr = a2_bohr;
     ++h->param_gen;  // the damping parameters are kernel arguments of a captured graph
     return upload_pair_table(h);
+}
+
+d3_status d3_set_three_body(d3_handle* h, double s9, double alpha9, double rc3_A) {
+    if (!h) return D3_ERR_ARG;
+    if (!std::isfinite(s9)) return fail(h, D3_ERR_ARG, "non-finite s9");
+    if (s9 != 0.0) {
+        if (!(alpha9 > 0.0) || !(alpha9 <= 64.0)) return fail(h, D3_ERR_ARG, "alpha9 must lie in (0, 64]");
+        if (!(rc3_A > 0.0) || !(rc3_A <= h->prm.rc_cn_A))
+            return fail(h, D3_ERR_ARG, "rc3 must lie in (0, R_cn]: the triangles come from the CN lists");
+    }
+    if (h->last_stream) cudaStreamSynchronize(h->last_stream);
+    h->s9 = s9;
+    h->alpha9 = s9 != 0.0 ? alpha9 : 16.0;
+    h->rc3_A = s9 != 0.0 ? rc3_A : 0.0;
+    ++h->param_gen;  // kernel arguments of a captured graph
+    return D3_OK;
 }
 
 d3_status d3_set_graphs(d3_handle* h, int32_t on) {
@@ -836,6 +875,8 @@ d3_status d3_backward(d3_handle* h, int32_t B, const int64_t* offsets, const dou
                       double* dLdparams, double* dLdpos, void* stream) {
     d3_status s = check_batch_args(h, B, offsets, pos, types, cells, pbc);
     if (s != D3_OK) return s;
+    if (h->s9 != 0.0)
+        return fail(h, D3_ERR_ARG, "the backward differentiates the two-body model; disable the three-body term");
     cudaStream_t st = (cudaStream_t)stream;
     h->last_stream = st;
     if (B > 0 && !dLdE) return fail(h, D3_ERR_ARG, "NULL dLdE");
@@ -906,9 +947,9 @@ d3_status d3_profile_enable(d3_handle* h, int32_t on) {
 d3_status d3_profile_read(d3_handle* h, double* ms, int64_t* calls, int64_t* launches) {
     if (!h) return D3_ERR_ARG;
     for (auto& v : h->ev_pending) {
-        cudaError_t e = cudaEventSynchronize(v[6]);
+        cudaError_t e = cudaEventSynchronize(v[kStages]);
         if (e != cudaSuccess) return cuda_fail(h, e, "profile event");
-        for (int k = 0; k < 6; ++k) {
+        for (int k = 0; k < kStages; ++k) {
             float t = 0.f;
             if (cudaEventElapsedTime(&t, v[k], v[k + 1]) == cudaSuccess) {
                 h->prof_ms[k] += t;
@@ -918,7 +959,7 @@ d3_status d3_profile_read(d3_handle* h, double* ms, int64_t* calls, int64_t* lau
         for (cudaEvent_t x : v) h->ev_pool.push_back(x);
     }
     h->ev_pending.clear();
-    for (int k = 0; k < 6; ++k) {
+    for (int k = 0; k < kStages; ++k) {
         if (ms) ms[k] = h->prof_ms[k];
         if (calls) calls[k] = h->prof_calls[k];
     }
@@ -929,7 +970,7 @@ d3_status d3_profile_read(d3_handle* h, double* ms, int64_t* calls, int64_t* lau
 d3_status d3_profile_reset(d3_handle* h) {
     if (!h) return D3_ERR_ARG;
     d3_status s = d3_profile_read(h, nullptr, nullptr, nullptr);
-    for (int k = 0; k < 6; ++k) {
+    for (int k = 0; k < kStages; ++k) {
         h->prof_ms[k] = 0;
         h->prof_calls[k] = 0;
     }

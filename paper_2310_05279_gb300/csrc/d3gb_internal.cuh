@@ -136,6 +136,10 @@ struct Consts {
     double s6, s8, a1, a2;     // damping of Eq. 2 (a2 in bohr)
     int T, R, RP;
     int accumulate;            // add E, F, W into the outputs instead of overwriting them
+    // optional three-body (triple-dipole) term, off when atm == 0
+    int atm;
+    double s9, alpha9;         // strength and damping exponent
+    double rc3_2;              // every side of a triangle below rc3: rc3^2, bohr^2 (rc3 <= R_cn)
 };
 
 // ---- neighbour lists: one row of `cap` entries per atom (cap a multiple of 8),
@@ -211,10 +215,11 @@ struct Tabs {
     const int* nref;       // [T]
     const float4* rcpair;  // [T][T] k2 (Rcov_i + Rcov_j) as hi, lo and its square as hi, lo (bohr)
     const float2* exptab;  // [64] 2^(j/64) as FP32 hi, lo
+    const void* rtab;      // [T][T] real: damping radius R = a1 R0 + a2 of Eq. 2 (bohr), for the three-body term
 };
 
-// marks (optional): 6 events recorded before the CN pass and after the CN,
-// weight, dispersion, chain and finalize passes.
+// marks (optional): 7 events recorded before the CN pass and after the CN,
+// weight, dispersion, three-body, chain and finalize passes.
 // w_atom (optional, device double[N][9]): per-atom virial of Eq. 7, eV.
 cudaError_t launch_forward(const Work& w, const Consts& c, bool mixed, const Tabs& tabs, double* E, double* F,
                            double* W, double* e_atom, double* cn_out, double* w_atom, int B, cudaStream_t st,
@@ -222,6 +227,7 @@ cudaError_t launch_forward(const Work& w, const Consts& c, bool mixed, const Tab
 // Eq. 8 per atom: J_i = W_i . v_i (device arrays).
 cudaError_t launch_heat(int64_t n, const double* w_atom, const double* vel, double* J, cudaStream_t st);
 constexpr int kForwardLaunches = 5;  // kernels per forward pass (B > 0, N > 0): CN, dispersion, chain, 2 sums
+                                     // (one more with the three-body term)
 constexpr int kBuildLaunches = 15;   // kernels per neighbour build (N > 0): reset, wrap, images, 2 x 3 scan,
                                      // 2 scatter, sort, 2 fill, lists
 }  // namespace d3gb

@@ -459,7 +459,7 @@ def main():
         tf = fl * three_body["triangles"] / (three_body["three_body_ms"] * 1e-3) / 1e12
         three_body["flop_per_triangle"] = fl
         three_body["roofline"] = {"bound": "alu", "kernel": "k_atm", "achieved": tf, "peak": fp32_peak,
-                                  "unit": "TFLOP/s", "frac": tf / fp32_peak,
+                                  "unit": "TFLOP/s", "frac": tf / fp32_peak, "traffic": recorded_traffic("k_atm"),
                                   "algorithmic": f"{fl} FLOP per unique triangle x {three_body['triangles']:.4g}"}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -474,6 +474,11 @@ def main():
                                       "(jitter seed 1 + rank), no collective on the data path"},
             "roofline": roof,
             "stage_ms": stage_ms, "dominant_stage": dom,
+            "split": {"with_build": value,
+                      "without_build": job_value(N, world, max(1e-9, ms - stage_ms["build"]) * 1e-3),
+                      "unit": UNIT,
+                      "how": "the timed step minus the neighbour-build stage of the profiled pass (the build "
+                             "runs in every timed step; with a skin it is amortised over the steps between rebuilds)"},
             "fp64_form": fp64,
             "three_body": three_body,
             "e2e": e2e,

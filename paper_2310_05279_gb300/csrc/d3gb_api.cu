@@ -195,6 +195,10 @@ Consts make_consts(const d3_handle* h) {
     c.alpha9 = h->alpha9;
     const double r3 = h->rc3_A / kBohrA;
     c.rc3_2 = r3 * r3;
+    c.s9f = (float)c.s9;
+    c.alpha9f = (float)c.alpha9;
+    c.alpha9_3f = (float)(c.alpha9 / 3.0);
+    c.rc3_2f = (float)c.rc3_2;
     return c;
 }
 

@@ -140,6 +140,7 @@ struct Consts {
     int atm;
     double s9, alpha9;         // strength and damping exponent
     double rc3_2;              // every side of a triangle below rc3: rc3^2, bohr^2 (rc3 <= R_cn)
+    float s9f, alpha9f, alpha9_3f, rc3_2f;  // FP32 copies (alpha9_3f = alpha9 / 3) for the mixed form
 };
 
 // ---- neighbour lists: one row of `cap` entries per atom (cap a multiple of 8),

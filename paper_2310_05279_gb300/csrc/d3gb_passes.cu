@@ -668,6 +668,31 @@ constexpr int kAtmQueue = 64;  // triangle queue per warp (ring; at most 63 entr
 
 template <bool MIXED> struct AtmCap { static constexpr int C = MIXED ? 128 : 64; };
 
+// Per-lane running sums of the three-body pass.  The mixed form keeps a
+// compensated float pair (value hi + lo) on the FP32 pipe: GB300 executes FP64
+// at 1/64 of the FP32 rate, so FP64 running sums and an FP64 warp reduction
+// would bound the kernel.  The FP64 form sums in FP64.
+template <bool MIXED> struct AtmAcc;
+template <> struct AtmAcc<true> {
+    float h = 0.f, l = 0.f;
+    __device__ void add(float x) { acc_add(h, l, x); }
+    // with the partner lane's sum (the same result on both lanes)
+    __device__ void xor_reduce(int o) {
+        const float h2 = __shfl_xor_sync(0xffffffffu, h, o), l2 = __shfl_xor_sync(0xffffffffu, l, o);
+        float sh, e;
+        two_sum(h, h2, sh, e);
+        h = sh;
+        l = (l + l2) + e;
+    }
+    __device__ float total() const { return h + l; }
+};
+template <> struct AtmAcc<false> {
+    double h = 0.0;
+    __device__ void add(double x) { h += x; }
+    __device__ void xor_reduce(int o) { h += __shfl_xor_sync(0xffffffffu, h, o); }
+    __device__ double total() const { return h; }
+};
+
 __device__ __forceinline__ float ex2_approx(float x) {
     float r;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
@@ -719,8 +744,10 @@ __global__ void __launch_bounds__(32 * kAtmWarps) k_atm(Work w, Consts c, const 
     const StructGeo& G = w.geo[w.sid[p]];
     const int* row = w.nbr_cn + list_row(G.list_base_cn, p - G.atom_base, G.cap_cn);
     const int cnt = w.cnt_cn[p];
-    const T rc3 = (T)c.rc3_2, s9 = (T)c.s9, alpha = (T)c.alpha9, a3 = (T)(c.alpha9 / 3.0);
-    double E = 0, Dn = 0, Fx = 0, Fy = 0, Fz = 0, V[6] = {0, 0, 0, 0, 0, 0};
+    // FP32 copies from the host in the mixed form (a conversion is an FP64-pipe operation)
+    const T rc3 = MIXED ? (T)c.rc3_2f : (T)c.rc3_2, s9 = MIXED ? (T)c.s9f : (T)c.s9;
+    const T alpha = MIXED ? (T)c.alpha9f : (T)c.alpha9, a3 = MIXED ? (T)c.alpha9_3f : (T)(c.alpha9 / 3.0);
+    AtmAcc<MIXED> aE, aDn, aFx, aFy, aFz, aV[6];
     T e_ = 0, dn_ = 0, fx_ = 0, fy_ = 0, fz_ = 0, v_[6] = {0, 0, 0, 0, 0, 0};  // FP32 partial sums
     int head = 0, tail = 0;  // queue positions (warp-uniform)
 
@@ -820,13 +847,13 @@ __global__ void __launch_bounds__(32 * kAtmWarps) k_atm(Work w, Consts c, const 
         v_[5] = fma(gy, Aj.z, fma(hy, Ak.z, v_[5]));
     };
     auto flush = [&]() {
-        E += (double)e_;
-        Dn += (double)dn_;
-        Fx += (double)fx_;
-        Fy += (double)fy_;
-        Fz += (double)fz_;
+        aE.add(e_);
+        aDn.add(dn_);
+        aFx.add(fx_);
+        aFy.add(fy_);
+        aFz.add(fz_);
 #pragma unroll
-        for (int m = 0; m < 6; ++m) V[m] += (double)v_[m];
+        for (int m = 0; m < 6; ++m) aV[m].add(v_[m]);
         e_ = dn_ = fx_ = fy_ = fz_ = 0;
 #pragma unroll
         for (int m = 0; m < 6; ++m) v_[m] = 0;
@@ -922,27 +949,33 @@ __global__ void __launch_bounds__(32 * kAtmWarps) k_atm(Work w, Consts c, const 
             }
         }
     }
-    // fixed-order warp sums
+    // fixed-order warp sums (every lane ends with the totals); lanes 0-7 each
+    // write one part of atom i's results
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        E += __shfl_xor_sync(0xffffffffu, E, o);
-        Dn += __shfl_xor_sync(0xffffffffu, Dn, o);
-        Fx += __shfl_xor_sync(0xffffffffu, Fx, o);
-        Fy += __shfl_xor_sync(0xffffffffu, Fy, o);
-        Fz += __shfl_xor_sync(0xffffffffu, Fz, o);
+        aE.xor_reduce(o);
+        aDn.xor_reduce(o);
+        aFx.xor_reduce(o);
+        aFy.xor_reduce(o);
+        aFz.xor_reduce(o);
 #pragma unroll
-        for (int m = 0; m < 6; ++m) V[m] += __shfl_xor_sync(0xffffffffu, V[m], o);
+        for (int m = 0; m < 6; ++m) aV[m].xor_reduce(o);
     }
-    if (lane != 0) return;
-    w.eat[p] += E / 3.0;
-    double* wv = w.wv + 6 * p;
+    // (the mixed form rounds the totals to FP32: its F and dE/dn are FP32 anyway,
+    // and the three-body site energy and virial are small parts of FP64 sums)
+    if (lane == 0) {
+        w.eat[p] += (double)(aE.total() * (T)(1.0 / 3.0));
+        T4* fd = (T4*)w.Fd + p;
+        const T4 f0 = *fd;
+        *fd = T4{f0.x + (T)2 * aFx.total(), f0.y + (T)2 * aFy.total(), f0.z + (T)2 * aFz.total(), f0.w};
+    } else if (lane == 1) {
+        T* dn = (T*)w.dEdn + p;
+        *dn += aDn.total();
+    } else {
 #pragma unroll
-    for (int m = 0; m < 6; ++m) wv[m] -= V[m];
-    T4* fd = (T4*)w.Fd + p;
-    const T4 f0 = *fd;
-    *fd = T4{(T)((double)f0.x + 2.0 * Fx), (T)((double)f0.y + 2.0 * Fy), (T)((double)f0.z + 2.0 * Fz), f0.w};
-    T* dn = (T*)w.dEdn + p;
-    *dn = (T)((double)*dn + Dn);
+        for (int m = 0; m < 6; ++m)
+            if (lane == 2 + m) w.wv[6 * p + m] -= (double)aV[m].total();
+    }
 }
 
 // ------------------------------------------------------------------ per-structure sums

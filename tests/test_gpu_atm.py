@@ -162,3 +162,51 @@ def test_argument_checks(torch_cuda):
     dLdF = torch.zeros((b.natoms, 3), dtype=torch.float64, device="cuda")
     with pytest.raises(D3Error):
         d3.backward(pos, typ, b.offsets, b.cells, b.pbc, dLdE, dLdF)
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_with_skin_accumulate_and_single_entry(torch_cuda, oracle_mod, precision):
+    """The three-body term with list reuse (a skin: the CN lists are longer than
+    rc3 and reused while atoms move less than skin/2), in accumulate mode (Eq. 9
+    coupling), and through the one-structure entry point."""
+    import dataclasses
+    import torch
+    from paper_2310_05279_gb300 import D3
+    b0 = wl.uneven_batch(seed=23, nstruct=4, n_range=(80, 400))
+    p = dict(PRM, s9=1.0, alpha9=16.0, rc3=5.5)
+    d3 = D3(b0.tables, p, precision=precision, skin=1.0)
+    ok = assert_fp64_ok if precision == "fp64" else assert_mixed_ok
+    g = np.random.Generator(np.random.PCG64(6))
+    pos = b0.pos
+    builds = []
+    for it in range(3):
+        b = dataclasses.replace(b0, pos=pos)
+        pt, tt = to_dev(b)
+        out = d3.compute_batch(pt, tt, b.offsets, b.cells, b.pbc)
+        d3.sync_status()
+        ok(out, oracle_mod.compute_batch(b, p), b.offsets)
+        builds.append(d3.build_count())
+        pos = pos + g.uniform(-0.15, 0.15, pos.shape)
+    assert builds[2] == builds[0]  # moves below skin/2: the lists were reused
+    # accumulate: E, F, W added onto a previous model's values
+    b = dataclasses.replace(b0, pos=pos)
+    pt, tt = to_dev(b)
+    ref = oracle_mod.compute_batch(b, p)
+    base = dict(E=torch.full((b.nstruct,), 1.5, dtype=torch.float64, device="cuda"),
+                F=torch.full((b.natoms, 3), -0.25, dtype=torch.float64, device="cuda"),
+                W=torch.full((b.nstruct, 3, 3), 0.75, dtype=torch.float64, device="cuda"))
+    d3.set_accumulate(True)
+    out = d3.compute_batch(pt, tt, b.offsets, b.cells, b.pbc, out={k: v.clone() for k, v in base.items()})
+    d3.sync_status()
+    d3.set_accumulate(False)
+    ok({k: out[k] - base[k] for k in ("E", "F", "W")}, ref, b.offsets)
+    # one structure through d3_compute
+    s = 1
+    ps, ts, cell, pbc = b.structure(s)
+    o1 = d3.compute(torch.tensor(ps, device="cuda"), torch.tensor(ts, dtype=torch.int32, device="cuda"), cell, pbc)
+    d3.sync_status()
+    r1 = oracle_mod.compute(ps, ts, cell, pbc, b.tables, p)
+    n = len(ps)
+    tol_e = 1e-11 * abs(r1["E"]) if precision == "fp64" else 1e-7 * n
+    assert abs(o1["E"].item() - r1["E"]) <= tol_e
+    assert np.abs(o1["F"].cpu().numpy() - r1["F"]).max() <= (1e-10 if precision == "fp64" else 1e-5)

@@ -225,6 +225,9 @@ struct Tabs {
 cudaError_t launch_forward(const Work& w, const Consts& c, bool mixed, const Tabs& tabs, double* E, double* F,
                            double* W, double* e_atom, double* cn_out, double* w_atom, int B, cudaStream_t st,
                            cudaEvent_t* marks);
+// Optional three-body pass (d3gb_atm.cu): adds into w.eat, w.wv, w.Fd and
+// w.dEdn after the dispersion pass; rtab as Tabs::rtab in the handle's precision.
+cudaError_t launch_atm(const Work& w, const Consts& c, bool mixed, const void* rtab, cudaStream_t st);
 // Eq. 8 per atom: J_i = W_i . v_i (device arrays).
 cudaError_t launch_heat(int64_t n, const double* w_atom, const double* vel, double* J, cudaStream_t st);
 constexpr int kForwardLaunches = 5;  // kernels per forward pass (B > 0, N > 0): CN, dispersion, chain, 2 sums

@@ -359,6 +359,25 @@ def perturbed_damping(seed: int = 4, base: Optional[dict] = None) -> dict:
     return base
 
 
+KB_EV = 8.617333262e-5          # Boltzmann constant, eV/K
+EV_PER_AMU_A2_FS2 = 103.6427      # 1 amu A^2 / fs^2 in eV (so 1 eV/amu = 9.6485e-3 A^2/fs^2)
+
+
+def atom_masses(batch: "Batch") -> np.ndarray:
+    """Mass (u) of every atom, from the element names of the batch's tables."""
+    return np.array([MASS[batch.tables.names[t]] for t in batch.types], np.float64)
+
+
+def maxwell_velocities(masses: np.ndarray, T_K: float, seed: int) -> np.ndarray:
+    """Velocities (A/fs) drawn from the Maxwell-Boltzmann distribution at T_K
+    (each component normal with variance kB T / m), centre-of-mass motion removed."""
+    g = _rng(seed)
+    sigma = np.sqrt(KB_EV * T_K / masses / EV_PER_AMU_A2_FS2)
+    v = g.normal(size=(len(masses), 3)) * sigma[:, None]
+    v -= (masses[:, None] * v).sum(0) / masses.sum()
+    return v
+
+
 def displacement_direction(n: int, seed: int) -> np.ndarray:
     """Unit-scale random direction field (N x 3), e.g. for tangent checks."""
     return _rng(seed).normal(size=(n, 3))

@@ -8,6 +8,8 @@
   the mixed form against the FP64 form (itself oracle-exact at smaller sizes).
 * 512-structure uneven batch: sampled structures of every size class against
   the oracle; all structures mixed against FP64.
+* the scan with the optional three-body term: every structure mixed against
+  FP64, 16 structures against the oracle.
 """
 import numpy as np
 import pytest
@@ -91,3 +93,38 @@ def test_uneven_batch_full(torch_cuda, oracle_mod):
                      "W": torch_cuda.tensor(mixed["W"][sample])}, ref, sub.offsets)
     assert_fp64_ok({"E": torch_cuda.tensor(fp64["E"][sample]), "F": torch_cuda.tensor(F64),
                     "W": torch_cuda.tensor(fp64["W"][sample])}, ref, sub.offsets)
+
+
+def test_bilayer_scan_full_three_body(torch_cuda, oracle_mod):
+    """The bench's three-body leg (mixed, s9 = 1, alpha = 16, rc3 = 6 A) on the full
+    128 x 1440 scan, in one batched call as timed; 16 structures spread over the
+    distance / slide grid against the oracle, all against the FP64 form."""
+    p = dict(PRM, s9=1.0, alpha9=16.0, rc3=6.0)
+    b = wl.bilayer_scan()
+    from paper_2310_05279_gb300 import D3
+    pos, typ = to_dev(b)
+    out = {}
+    for prec in ("mixed", "fp64"):
+        d3 = D3(b.tables, p, precision=prec)
+        r = d3.compute_batch(pos, typ, b.offsets, b.cells, b.pbc)
+        d3.sync_status()
+        out[prec] = {k: v.cpu().numpy() for k, v in r.items()}
+        del d3
+    m, f = out["mixed"], out["fp64"]
+    n = np.diff(b.offsets)
+    assert (np.abs(m["E"] - f["E"]) / n).max() <= TOL_E_PER_ATOM
+    assert np.abs(m["F"] - f["F"]).max() <= TOL_F_MAX
+    wn = np.linalg.norm(f["W"].reshape(-1, 9), axis=1)
+    assert (np.linalg.norm((m["W"] - f["W"]).reshape(-1, 9), axis=1) / wn).max() <= TOL_W_REL
+    sample = list(range(0, 128, 8))
+    sub = b.subset(sample)
+    ref = oracle_mod.compute_batch(sub, p)
+    F = np.concatenate([m["F"][b.offsets[s]:b.offsets[s + 1]] for s in sample])
+    F64 = np.concatenate([f["F"][b.offsets[s]:b.offsets[s + 1]] for s in sample])
+    assert_mixed_ok({"E": torch_cuda.tensor(m["E"][sample]), "F": torch_cuda.tensor(F),
+                     "W": torch_cuda.tensor(m["W"][sample])}, ref, sub.offsets)
+    assert_fp64_ok({"E": torch_cuda.tensor(f["E"][sample]), "F": torch_cuda.tensor(F64),
+                    "W": torch_cuda.tensor(f["W"][sample])}, ref, sub.offsets)
+    # the three-body term raises the energy of every sampled structure (in-plane triangles dominate)
+    E2 = oracle_mod.compute_batch(sub, PRM)["E"]
+    assert np.all(ref["E"] > E2)

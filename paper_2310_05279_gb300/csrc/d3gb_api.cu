@@ -80,6 +80,8 @@ struct d3_handle {
     DevBuf tabmem;
     int* d_nref = nullptr;
     double* d_cnref = nullptr;
+    float2* d_cnref2 = nullptr;  // reference CNs as FP32 hi, lo
+    float* d_dcr = nullptr;      // [T][R][R] differences of reference CNs, FP32
     float* d_c6f = nullptr;
     double* d_c6d = nullptr;
     float4* d_pairf = nullptr;
@@ -195,6 +197,11 @@ Consts make_consts(const d3_handle* h) {
     c.alpha9 = h->alpha9;
     const double r3 = h->rc3_A / kBohrA;
     c.rc3_2 = r3 * r3;
+    c.k1f = (float)c.k1;
+    c.rc_cn2f = (float)c.rc_cn2;
+    c.k3f = (float)c.k3;
+    c.k3h = (float)c.k3;
+    c.k3l = (float)(c.k3 - (double)c.k3h);
     c.s9f = (float)c.s9;
     c.alpha9f = (float)c.alpha9;
     c.alpha9_3f = (float)(c.alpha9 / 3.0);
@@ -265,6 +272,13 @@ d3_status plan_geometry(d3_handle* h, Plan& P, int32_t B, const int64_t* offsets
             nc_total *= nck;
         }
         if (nc_total > ((int64_t)1 << 26)) return fail(h, D3_ERR_ARG, "too many cells for structure " + std::to_string(s));
+        for (int k = 0; k < 9; ++k) G.Hinvf[k] = (float)G.Hinv[k];
+        for (int k = 0; k < 3; ++k) {
+            G.lof[k] = (float)G.lo[k];
+            G.fscalef[k] = (float)G.fscale[k];
+            G.ext_lof[k] = (float)G.ext_lo[k];
+            G.ext_hif[k] = (float)G.ext_hi[k];
+        }
         G.cell_base = cell_base;
         cell_base += nc_total;
         G.atom_base = offsets[s];
@@ -343,7 +357,7 @@ d3_status plan_alloc(d3_handle* h, Plan& P) {
     A(w.pos64, dbl4, Nt);
     A(w.rec, float4, 2 * Nt);
     A(w.hi, float4, Nt);
-    A(w.fw, double, 3 * Nr);
+    A(w.fw, float, 3 * Nr);
     A(w.frange, int, 6 * (int64_t)B);
     A(w.perm, int, Nr);
     A(w.sid, int, Nr);
@@ -550,6 +564,8 @@ d3_status forward(d3_handle* h, int32_t B, const int64_t* offsets, const double*
     tb.c6 = mixed ? (const void*)h->d_c6f : (const void*)h->d_c6d;
     tb.pair = mixed ? (const void*)h->d_pairf : (const void*)h->d_paird;
     tb.cnref = h->d_cnref;
+    tb.cnref2 = h->d_cnref2;
+    tb.dcr = h->d_dcr;
     tb.nref = h->d_nref;
     tb.rcpair = h->d_rcpair;
     tb.exptab = h->d_exptab;
@@ -683,6 +699,8 @@ d3_status d3_create(const d3_params* params, const d3_tables* tables, d3_handle*
     DevBuf& m = h->tabmem;
     if (e == cudaSuccess) e = m.alloc(&h->d_nref, T);
     if (e == cudaSuccess) e = m.alloc(&h->d_cnref, T * R);
+    if (e == cudaSuccess) e = m.alloc(&h->d_cnref2, T * R);
+    if (e == cudaSuccess) e = m.alloc(&h->d_dcr, T * R * R);
     if (e == cudaSuccess) e = m.alloc(&h->d_c6f, h->c6.size());
     if (e == cudaSuccess) e = m.alloc(&h->d_c6d, h->c6.size());
     if (e == cudaSuccess) e = m.alloc(&h->d_pairf, T * T);
@@ -697,6 +715,20 @@ d3_status d3_create(const d3_params* params, const d3_tables* tables, d3_handle*
     if (e == cudaSuccess) e = m.alloc(&h->d_nbuild, 1);
     if (e == cudaSuccess) e = cudaMemcpy(h->d_nref, h->nref.data(), T * sizeof(int), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(h->d_cnref, h->cnref.data(), T * R * sizeof(double), cudaMemcpyHostToDevice);
+    {
+        std::vector<float2> cr2(T * R);
+        std::vector<float> dcr((size_t)T * R * R);
+        for (int a = 0; a < T; ++a)
+            for (int i = 0; i < R; ++i) {
+                const double v = h->cnref[a * R + i];
+                const float hi = (float)v;
+                cr2[a * R + i] = make_float2(hi, (float)(v - (double)hi));
+                for (int j = 0; j < R; ++j)
+                    dcr[((size_t)a * R + i) * R + j] = (float)(h->cnref[a * R + j] - h->cnref[a * R + i]);
+            }
+        if (e == cudaSuccess) e = cudaMemcpy(h->d_cnref2, cr2.data(), cr2.size() * sizeof(float2), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(h->d_dcr, dcr.data(), dcr.size() * sizeof(float), cudaMemcpyHostToDevice);
+    }
     if (e == cudaSuccess) e = cudaMemcpy(h->d_c6f, c6f.data(), c6f.size() * sizeof(float), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(h->d_c6d, h->c6.data(), h->c6.size() * sizeof(double), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(h->d_rk, rk.data(), T * sizeof(double), cudaMemcpyHostToDevice);

@@ -24,19 +24,32 @@ namespace {
 // A build kernel does nothing when list reuse is on and no atom has moved enough.
 __device__ __forceinline__ bool skip_build(const Work& w) { return w.gate && *w.gate == 0; }
 
-__device__ inline int cell_id(const StructGeo& G, const double f[3]) {
+// The binning, wrap and image decisions below are taken in FP32: GB300 runs
+// FP64 at 1/64 of the FP32 rate, and the list radius carries a margin (4e-3
+// bohr plus 1e-5 relative) far above their rounding (about 3e-5 bohr at 500
+// bohr), so an atom binned one cell off, or an image kept or dropped at the
+// edge of its window, changes no pair within the cutoffs.  Positions
+// themselves stay FP64.
+__device__ inline int cell_id(const StructGeo& G, const float f[3]) {
     int c[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        double u = (f[k] - G.lo[k]) * G.fscale[k];
-        u = fmin(fmax(u, 0.0), (double)(G.ncell[k] - 1));
+        float u = (f[k] - G.lof[k]) * G.fscalef[k];
+        u = fminf(fmaxf(u, 0.0f), (float)(G.ncell[k] - 1));
         c[k] = (int)u;
     }
     return (int)(G.cell_base + ((int64_t)c[2] * G.ncell[1] + c[1]) * G.ncell[0] + c[0]);
 }
 
+__device__ __forceinline__ bool finite_bits(double x) {
+    return (__double_as_longlong(x) & 0x7ff0000000000000LL) != 0x7ff0000000000000LL;
+}
+
 // Wrap into the cell, bin, and record each structure's occupied fractional
-// range per periodic axis (as float bits: the fractions are >= 0).
+// range per periodic axis (as float bits: the fractions are >= 0).  The
+// lattice translation that wraps an atom is chosen from its FP32 fractional
+// coordinates; the wrapped position is x - sum_k n_k H_k in FP64 (x itself
+// when the atom is inside the cell).
 __global__ void __launch_bounds__(256) k_wrap(Work w, const double* __restrict__ pos, const int32_t* __restrict__ types) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= w.Nr || skip_build(w)) return;
@@ -47,7 +60,7 @@ __global__ void __launch_bounds__(256) k_wrap(Work w, const double* __restrict__
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         xb[a] = pos[3 * i + a] * (1.0 / kBohrA);
-        fin = fin && isfinite(xb[a]);
+        fin = fin && finite_bits(xb[a]);
     }
     if (!fin) {
         atomicOr(w.status, ST_NONFINITE);
@@ -55,23 +68,35 @@ __global__ void __launch_bounds__(256) k_wrap(Work w, const double* __restrict__
     }
     const int t = types[i];
     if (t < 0 || t >= w.T) atomicOr(w.status, ST_TYPE);
-    double f[3];
+    const float xf[3] = {(float)xb[0], (float)xb[1], (float)xb[2]};
+    float f[3];
+    int n[3] = {0, 0, 0};
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        f[k] = xb[0] * G.Hinv[k] + xb[1] * G.Hinv[3 + k] + xb[2] * G.Hinv[6 + k];
+        f[k] = xf[0] * G.Hinvf[k] + xf[1] * G.Hinvf[3 + k] + xf[2] * G.Hinvf[6 + k];
         if (G.pbc[k]) {
-            f[k] -= floor(f[k]);
-            if (f[k] >= 1.0) f[k] -= 1.0;
+            const float fl = floorf(f[k]);
+            n[k] = (int)fl;
+            f[k] -= fl;  // exact, in [0, 1]
+            if (f[k] >= 1.0f) {
+                f[k] = 0.0f;
+                n[k] += 1;
+            }
         }
         w.fw[3 * i + k] = f[k];
     }
+    double xw[3] = {xb[0], xb[1], xb[2]};
+    if (n[0] | n[1] | n[2]) {
+        const double n0 = n[0], n1 = n[1], n2 = n[2];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) xw[a] = xb[a] - (n0 * G.H[a] + n1 * G.H[3 + a] + n2 * G.H[6 + a]);
+    }
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const double xw = f[0] * G.H[a] + f[1] * G.H[3 + a] + f[2] * G.H[6 + a];
-        w.xw[3 * i + a] = xw;
+        w.xw[3 * i + a] = xw[a];
         if (w.skin_half2 > 0.0) {  // references for list reuse
             w.xref[3 * i + a] = xb[a];
-            w.wshift[3 * i + a] = xw - xb[a];
+            w.wshift[3 * i + a] = xw[a] - xb[a];
         }
     }
     const int cid = cell_id(G, f);
@@ -83,8 +108,8 @@ __global__ void __launch_bounds__(256) k_wrap(Work w, const double* __restrict__
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         if (!G.pbc[k]) continue;
-        const int lo = __reduce_min_sync(grp, __float_as_int(__double2float_rd(f[k])));
-        const int hi = __reduce_max_sync(grp, __float_as_int(__double2float_ru(f[k])));
+        const int lo = __reduce_min_sync(grp, __float_as_int(f[k]));
+        const int hi = __reduce_max_sync(grp, __float_as_int(f[k]));
         if (leader) {
             atomicMin(&w.frange[3 * s + k], lo);
             atomicMax(&w.frange[3 * (w.B + s) + k], hi);
@@ -102,20 +127,20 @@ __global__ void __launch_bounds__(256) k_images(Work w) {
     const bool live = i < w.Nr;
     const int s = live ? w.sid_in[i] : 0;
     const StructGeo& G = w.geo[s];
-    double f[3] = {0, 0, 0};
+    float f[3] = {0, 0, 0};
     int nlo[3] = {0, 0, 0}, nhi[3] = {0, 0, 0};
-    double u0[3] = {0, 0, 0};
+    float u0[3] = {0, 0, 0};
     if (live) {
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             f[k] = w.fw[3 * i + k];
-            u0[k] = (f[k] - G.lo[k]) * G.fscale[k];
+            u0[k] = (f[k] - G.lof[k]) * G.fscalef[k];
             if (G.img[k] > 0) {
-                const double delta = G.ext_hi[k] - 1.0;
-                const double omin = (double)__int_as_float(w.frange[3 * s + k]);
-                const double omax = (double)__int_as_float(w.frange[3 * (w.B + s) + k]);
-                nlo[k] = max(-G.img[k], (int)ceil(fmax(G.ext_lo[k], omin - delta) - f[k]));
-                nhi[k] = min(G.img[k], min((int)ceil(G.ext_hi[k] - f[k]) - 1, (int)floor(omax + delta - f[k])));
+                const float delta = G.ext_hif[k] - 1.0f;
+                const float omin = __int_as_float(w.frange[3 * s + k]);
+                const float omax = __int_as_float(w.frange[3 * (w.B + s) + k]);
+                nlo[k] = max(-G.img[k], (int)ceilf(fmaxf(G.ext_lof[k], omin - delta) - f[k]));
+                nhi[k] = min(G.img[k], min((int)ceilf(G.ext_hif[k] - f[k]) - 1, (int)floorf(omax + delta - f[k])));
             }
         }
     }
@@ -150,7 +175,7 @@ __global__ void __launch_bounds__(256) k_images(Work w) {
     if (!live || mine <= 0) return;
     int slot = base + wsum[wid] + x - mine;
     auto cell_of_axis = [&](int k, int n) {
-        const int c = (int)floor(u0[k] + n * G.fscale[k]);
+        const int c = (int)floorf(u0[k] + (float)n * G.fscalef[k]);
         return min(max(c, 0), G.ncell[k] - 1);
     };
     for (int n0 = nlo[0]; n0 <= nhi[0]; ++n0) {
@@ -389,14 +414,23 @@ __global__ void __launch_bounds__(256) k_check(Work w, const double* __restrict_
 // Split position: hi on a 2^-10 bohr grid (exact in FP32 for |x| < 2^13 bohr),
 // lo = x - hi (|lo| <= 2^-11).  Differences of hi parts are then exact in
 // FP32, so a pair vector is recovered as D + e with no rounding lost.
+// hi is the grid point nearest x, found from the float pair x = xh + xl (xl
+// exact to 2^-24 |xh|) without FP64 products: m = rint(1024 xh), then the
+// remainder 1024 (xh - m/1024) + 1024 xl, exact in FP32 below 2^-10 by
+// Sterbenz, moves m by one when it exceeds 1/2.
 __device__ inline void store_pos(Work& w, int64_t q, const double x[3], double rk, int tsrc) {
     w.pos64[q] = dbl4_make(x[0], x[1], x[2], rk);
     float h[3], l[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const double g = rint(x[a] * 1024.0) * (1.0 / 1024.0);
-        h[a] = (float)g;
-        l[a] = (float)(x[a] - (double)h[a]);
+        const float xh = (float)x[a];
+        const float xl = (float)(x[a] - (double)xh);
+        float m = rintf(xh * 1024.0f);
+        const float r = (xh * 1024.0f - m) + xl * 1024.0f;
+        if (r > 0.5f) m += 1.0f;
+        else if (r < -0.5f) m -= 1.0f;
+        h[a] = m * (1.0f / 1024.0f);
+        l[a] = (xh - h[a]) + xl;
     }
     w.rec[2 * q] = make_float4(h[0], h[1], h[2], __int_as_float(tsrc));
     w.rec[2 * q + 1] = make_float4(l[0], l[1], l[2], (float)rk);

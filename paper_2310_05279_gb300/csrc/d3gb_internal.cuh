@@ -49,6 +49,9 @@ struct StructGeo {
     double lo[3];     // fractional coordinate of the grid origin along each axis
     double fscale[3]; // grid cells per unit of fractional coordinate
     double ext_lo[3], ext_hi[3];  // fractional window of image atoms (periodic axes)
+    // FP32 copies for the binning and image decisions (the list radius margin
+    // covers their rounding): inverse cell, grid origin and scale, image window
+    float Hinvf[9], lof[3], fscalef[3], ext_lof[3], ext_hif[3];
     int ncell[3];
     int win[3];       // window half-width (cells) covering the list radius
     int img[3];       // image range, 0 along open axes
@@ -92,7 +95,7 @@ struct Work {
     dbl4* pos64;             // [Nr + ghost_cap]
     float4* rec;             // [2 * (Nr + ghost_cap)]: hi at 2q, lo at 2q + 1
     float4* hi;              // [Nr + ghost_cap] compact copy of the hi parts for the list build
-    double* fw;              // [Nr * 3] wrapped fractional coordinates, input order
+    float* fw;               // [Nr * 3] wrapped fractional coordinates (FP32), input order
     int* frange;             // [2][B][3] float bits: min and max occupied fraction per axis
     int* perm;               // [Nr] sorted -> input index
     int* sid;                // [Nr] structure of sorted real atom
@@ -141,6 +144,8 @@ struct Consts {
     double s9, alpha9;         // strength and damping exponent
     double rc3_2;              // every side of a triangle below rc3: rc3^2, bohr^2 (rc3 <= R_cn)
     float s9f, alpha9f, alpha9_3f, rc3_2f;  // FP32 copies (alpha9_3f = alpha9 / 3) for the mixed form
+    float k1f, rc_cn2f, k3f;   // FP32 copies for the mixed form
+    float k3h, k3l;            // k3 as a float pair (k3h + k3l)
 };
 
 // ---- neighbour lists: one row of `cap` entries per atom (cap a multiple of 8),
@@ -216,6 +221,8 @@ struct Tabs {
     const int* nref;       // [T]
     const float4* rcpair;  // [T][T] k2 (Rcov_i + Rcov_j) as hi, lo and its square as hi, lo (bohr)
     const float2* exptab;  // [64] 2^(j/64) as FP32 hi, lo
+    const float2* cnref2;  // [T][R] reference CNs as FP32 hi, lo
+    const float* dcr;      // [T][R][R] cnref[t][b] - cnref[t][a], rounded to FP32
     const void* rtab;      // [T][T] real: damping radius R = a1 R0 + a2 of Eq. 2 (bohr), for the three-body term
 };
 

@@ -171,6 +171,29 @@ __device__ __forceinline__ void store_row(T* dst, const T (&v)[8], int rp) {
     if (rp > 4) d[1] = T4{v[4], v[5], v[6], v[7]};
 }
 
+// W and dW/dn rows of atom p and its projections v_p^(u)_a = sum_b C6ref[u][t][a][b] W_b
+template <class T, int R>
+__device__ __forceinline__ void store_weights(const Work& w, const Consts& c, const T* __restrict__ c6, int64_t p, int t,
+                                              const T (&L)[R], const T (&Wr)[8], const T (&dWr)[8]) {
+    store_row<T>((T*)w.W + p * c.RP, Wr, c.RP);
+    store_row<T>((T*)w.dW + p * c.RP, dWr, c.RP);
+    T* vp = (T*)w.v + p * c.T * c.RP;
+    for (int u = 0; u < c.T; ++u) {
+        const T* cu = c6 + ((size_t)(u * c.T + t) * R) * R;  // C6ref[u][t][a][b]
+        T vr[8];
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+            T s = 0;
+            if (a < R) {
+#pragma unroll
+                for (int b = 0; b < R; ++b) s += cu[a * R + b] * L[b];
+            }
+            vr[a] = s;
+        }
+        store_row<T>(vp + u * c.RP, vr, c.RP);
+    }
+}
+
 template <bool MIXED, int R>
 __device__ __forceinline__ void weights_atom(const Work& w, const Consts& c, const double* __restrict__ cnref,
                                              const int* __restrict__ nref,
@@ -220,23 +243,68 @@ __device__ __forceinline__ void weights_atom(const Work& w, const Consts& c, con
             Wr[a] = dWr[a] = 0;
         }
     }
-    store_row<T>((T*)w.W + p * c.RP, Wr, c.RP);
-    store_row<T>((T*)w.dW + p * c.RP, dWr, c.RP);
-    T* vp = (T*)w.v + p * c.T * c.RP;
-    for (int u = 0; u < c.T; ++u) {
-        const T* cu = c6 + ((size_t)(u * c.T + t) * R) * R;  // C6ref[u][t][a][b]
-        T vr[8];
+    store_weights<T, R>(w, c, c6, p, t, L, Wr, dWr);
+}
+
+// Mixed form of the above without FP64 (GB300 runs FP64 at 1/64 of the FP32
+// rate): the exponents -k3 (n - nref_a)^2 are formed in float-float from
+// n = Nh + Nl, nref_a = cnref2[t][a].x + .y and k3 = k3h + k3l, about 44
+// significant bits, so their absolute error stays far below the FP32 rounding
+// of exp itself; the differences nref_b - nref_a come from a host table
+// (dcr[t][a][b], rounded once).
+template <int R>
+__device__ __forceinline__ void weights_atom_mixed(const Work& w, const Consts& c, const float2* __restrict__ cnref2,
+                                                   const float* __restrict__ dcr, const int* __restrict__ nref,
+                                                   const float* __restrict__ c6, int64_t p, int t, float Nh,
+                                                   float Nl) {
+    const int nr = nref[t];
+    float xh[R], xl[R];
+    float mh = -3.0e38f, ml = 0.0f;
 #pragma unroll
-        for (int a = 0; a < 8; ++a) {
-            T s = 0;
-            if (a < R) {
-#pragma unroll
-                for (int b = 0; b < R; ++b) s += cu[a * R + b] * L[b];
-            }
-            vr[a] = s;
+    for (int a = 0; a < R; ++a) {
+        const float2 cr = cnref2[t * R + a];
+        float zh, ze, zl;
+        two_sum(Nh, -cr.x, zh, ze);
+        two_sum(zh, ze + (Nl - cr.y), zh, zl);  // z = n - nref_a
+        const float ph = zh * zh, pl = fmaf(zh, zh, -ph) + 2.0f * zh * zl;
+        xh[a] = -c.k3h * ph;
+        xl[a] = fmaf(-c.k3h, ph, -xh[a]) - c.k3h * pl - c.k3l * ph;
+        if (a < nr && (xh[a] > mh || (xh[a] == mh && xl[a] > ml))) {
+            mh = xh[a];
+            ml = xl[a];
         }
-        store_row<T>(vp + u * c.RP, vr, c.RP);
     }
+    float L[R];
+    float sum = 0.0f;
+#pragma unroll
+    for (int a = 0; a < R; ++a) {
+        L[a] = 0.0f;
+        if (a < nr) {
+            float yh, ye, yl;
+            two_sum(xh[a], -mh, yh, ye);
+            two_sum(yh, ye + (xl[a] - ml), yh, yl);
+            L[a] = expf(yh) * (1.0f + yl);
+        }
+        sum += L[a];
+    }
+    const float inv = 1.0f / sum;
+#pragma unroll
+    for (int a = 0; a < R; ++a) L[a] *= inv;
+    float Wr[8], dWr[8];
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+        if (a < R) {
+            float s = 0.0f;
+            const float* dr = dcr + (t * R + a) * R;
+#pragma unroll
+            for (int b = 0; b < R; ++b) s += L[b] * dr[b];
+            Wr[a] = L[a];
+            dWr[a] = -2.0f * c.k3f * L[a] * s;
+        } else {
+            Wr[a] = dWr[a] = 0.0f;
+        }
+    }
+    store_weights<float, R>(w, c, c6, p, t, L, Wr, dWr);
 }
 
 // ------------------------------------------------------------------ Eq. 4
@@ -248,6 +316,7 @@ __device__ __forceinline__ void weights_atom(const Work& w, const Consts& c, con
 template <bool MIXED, int R>
 __global__ void __launch_bounds__(128) k_cn(Work w, Consts c, const float4* __restrict__ rcpair,
                                            const float2* __restrict__ exptab, const double* __restrict__ cnref,
+                                           const float2* __restrict__ cnref2, const float* __restrict__ dcr,
                                            const int* __restrict__ nref,
                                            const typename Real<MIXED>::T* __restrict__ c6) {
     using T = typename Real<MIXED>::T;
@@ -257,7 +326,7 @@ __global__ void __launch_bounds__(128) k_cn(Work w, Consts c, const float4* __re
     const StructGeo& G = w.geo[w.sid[p]];
     const ListView LV{w.nbr_cn + list_row(G.list_base_cn, p - G.atom_base, G.cap_cn)};
     const int cnt = w.cnt_cn[p];
-    const T rc2 = (T)c.rc_cn2, k1 = (T)c.k1;
+    const T rc2 = MIXED ? (T)c.rc_cn2f : (T)c.rc_cn2, k1 = MIXED ? (T)c.k1f : (T)c.k1;
     T nh = 0, nl = 0;
     if constexpr (MIXED) {
         const float4* rrow = rcpair + (S.tsrc() & 15) * c.T;
@@ -276,9 +345,11 @@ __global__ void __launch_bounds__(128) k_cn(Work w, Consts c, const float4* __re
                 nl += z.fl;
             }
         });
-        const double n = (double)nint + (double)nh + (double)nl;
-        w.cn[p] = n;
-        weights_atom<MIXED, R>(w, c, cnref, nref, c6, p, S.tsrc() & 15, n);
+        float Nh, Nl;  // n = nint + nh + nl as a float pair
+        two_sum((float)nint, nh, Nh, Nl);
+        Nl += nl;
+        w.cn[p] = (double)Nh + (double)Nl;
+        weights_atom_mixed<R>(w, c, cnref2, dcr, nref, (const float*)c6, p, S.tsrc() & 15, Nh, Nl);
     } else {
         const T rki = S.rk();
         LV.for_each(0, cnt, [&](int q) {
@@ -405,7 +476,7 @@ __global__ void __launch_bounds__(128) k_chain(Work w, Consts c, const float4* _
     const StructGeo& G = w.geo[w.sid[p]];
     const ListView LV{w.nbr_cn + list_row(G.list_base_cn, p - G.atom_base, G.cap_cn)};
     const int cnt = w.cnt_cn[p];
-    const T rc2 = (T)c.rc_cn2, k1 = (T)c.k1;
+    const T rc2 = MIXED ? (T)c.rc_cn2f : (T)c.rc_cn2, k1 = MIXED ? (T)c.k1f : (T)c.k1;
     T fx = 0, fy = 0, fz = 0;
     double Sxx = 0, Syy = 0, Szz = 0, Sxy = 0, Sxz = 0, Syz = 0;
     double Tm[6] = {0, 0, 0, 0, 0, 0}, Gv[3] = {0, 0, 0}, Mm[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
@@ -589,7 +660,8 @@ cudaError_t forward_impl(const Work& w, const Consts& c, const Tabs& tb, double*
     };
     mark(0);
     if (w.Nr > 0)
-        k_cn<MIXED, R><<<nblk(w.Nr, TB), TB, 0, st>>>(w, c, tb.rcpair, tb.exptab, tb.cnref, tb.nref, (const T*)tb.c6);
+        k_cn<MIXED, R><<<nblk(w.Nr, TB), TB, 0, st>>>(w, c, tb.rcpair, tb.exptab, tb.cnref, tb.cnref2, tb.dcr, tb.nref,
+                                                      (const T*)tb.c6);
     mark(1);  // the weights (Eq. 3) are formed inside the CN pass
     mark(2);
     if (w.Nr > 0) {

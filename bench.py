@@ -87,10 +87,32 @@ def job_value(atoms_per_rank: int, world: int, seconds: float) -> float:
     return world * atoms_per_rank / seconds
 
 
+PAIR_HELPERS = "paper_2310_05279_gb300/csrc/d3gb_pair.cuh"  # device helpers inlined into the pair kernels
+
+
+def kernel_source_sha(path: str, kernel: str):
+    """SHA-256 of a kernel's definition in a CUDA source (from the line that
+    declares the __global__ function to the first closing brace in column 0)
+    together with the shared pair helpers it inlines."""
+    import hashlib
+    import re
+    with open(path) as f:
+        lines = f.read().split("\n")
+    with open(os.path.join(ROOT, PAIR_HELPERS)) as f:
+        helpers = f.read()
+    pat = re.compile(r"__global__.*\b" + re.escape(kernel) + r"\(")
+    for k, line in enumerate(lines):
+        if pat.search(line):
+            end = next((j for j in range(k, len(lines)) if lines[j] == "}"), None)
+            if end is None:
+                return None
+            return hashlib.sha256(("\n".join(lines[k:end + 1]) + "\n" + helpers).encode()).hexdigest()
+    return None
+
+
 def recorded_traffic(kernel: str):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, or None
-    when the kernel's source has changed since the counters were taken."""
-    import hashlib
+    when the kernel's definition has changed since the counters were taken."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
@@ -99,11 +121,8 @@ def recorded_traffic(kernel: str):
     if not rec:
         return None
     src = os.path.join(ROOT, rec["source"])
-    if not os.path.exists(src):
+    if not os.path.exists(src) or kernel_source_sha(src, kernel) != rec.get("kernel_sha256"):
         return None
-    with open(src, "rb") as f:
-        if hashlib.sha256(f.read()).hexdigest() != rec["sha256"]:
-            return None
     return float(rec["dram_bytes_per_launch"])
 
 

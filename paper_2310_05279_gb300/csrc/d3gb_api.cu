@@ -272,7 +272,12 @@ d3_status plan_geometry(d3_handle* h, Plan& P, int32_t B, const int64_t* offsets
             nc_total *= nck;
         }
         if (nc_total > ((int64_t)1 << 26)) return fail(h, D3_ERR_ARG, "too many cells for structure " + std::to_string(s));
-        for (int k = 0; k < 9; ++k) G.Hinvf[k] = (float)G.Hinv[k];
+        for (int k = 0; k < 9; ++k) {
+            G.Hinvf[k] = (float)G.Hinv[k];
+            const double g = std::nearbyint(G.H[k] * 1024.0) / 1024.0;
+            G.Hh[k] = (float)g;
+            G.Hl[k] = (float)(G.H[k] - g);
+        }
         for (int k = 0; k < 3; ++k) {
             G.lof[k] = (float)G.lo[k];
             G.fscalef[k] = (float)G.fscale[k];

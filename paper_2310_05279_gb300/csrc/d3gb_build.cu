@@ -451,6 +451,9 @@ __global__ void k_fill_real(Work w, const int32_t* __restrict__ types, const dou
     store_pos(w, p, x, rk_tab[t], t | ((int)p << 4));
 }
 
+// An image's FP64 position is its source's plus the lattice translation; its
+// split is the source's split plus the translation's (grid parts add exactly),
+// moved back to the nearest grid point (|lo| <= 2^-11) by whole grid steps.
 __global__ void k_fill_ghost(Work w, const int32_t* __restrict__ types, const double* __restrict__ rk_tab) {
     int q = blockIdx.x * blockDim.x + threadIdx.x;
     int ng = w.start_ghost[w.ncells];
@@ -462,10 +465,29 @@ __global__ void k_fill_ghost(Work w, const int32_t* __restrict__ types, const do
     const StructGeo& G = w.geo[w.ghost_sid[g]];
     int t = types[i];
     if (t < 0 || t >= w.T) t = 0;
+    const int ps = w.slot_of[i];  // the source's sorted slot (written by k_fill_real)
+    const double rk = rk_tab[t];
+    const double d0 = n0, d1 = n1, d2 = n2;
     double x[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) x[a] = w.xw[3 * i + a] + (n0 * G.H[a] + n1 * G.H[3 + a] + n2 * G.H[6 + a]);
-    store_pos(w, w.Nr + q, x, rk_tab[t], t | (w.slot_of[i] << 4));
+    for (int a = 0; a < 3; ++a) x[a] = w.xw[3 * i + a] + (d0 * G.H[a] + d1 * G.H[3 + a] + d2 * G.H[6 + a]);
+    w.pos64[w.Nr + q] = dbl4_make(x[0], x[1], x[2], rk);
+    const float4 hs = w.rec[2 * ps], ls = w.rec[2 * ps + 1];
+    const float f0 = (float)n0, f1 = (float)n1, f2 = (float)n2;
+    const float sh[3] = {hs.x, hs.y, hs.z}, sl[3] = {ls.x, ls.y, ls.z};
+    float h[3], l[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        h[a] = sh[a] + (f0 * G.Hh[a] + f1 * G.Hh[3 + a] + f2 * G.Hh[6 + a]);
+        l[a] = sl[a] + (f0 * G.Hl[a] + f1 * G.Hl[3 + a] + f2 * G.Hl[6 + a]);
+        const float m = rintf(l[a] * 1024.0f);
+        h[a] += m * (1.0f / 1024.0f);
+        l[a] -= m * (1.0f / 1024.0f);
+    }
+    const int tsrc = t | (ps << 4);
+    w.rec[2 * (w.Nr + q)] = make_float4(h[0], h[1], h[2], __int_as_float(tsrc));
+    w.rec[2 * (w.Nr + q) + 1] = make_float4(l[0], l[1], l[2], ls.w);
+    w.hi[w.Nr + q] = make_float4(h[0], h[1], h[2], 0.f);
 }
 
 // ---- per-atom lists within the two list radii ------------------------------

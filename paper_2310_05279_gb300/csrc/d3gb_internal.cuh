@@ -52,6 +52,8 @@ struct StructGeo {
     // FP32 copies for the binning and image decisions (the list radius margin
     // covers their rounding): inverse cell, grid origin and scale, image window
     float Hinvf[9], lof[3], fscalef[3], ext_lof[3], ext_hif[3];
+    // lattice rows split like positions: Hh on the 2^-10 bohr grid, Hl = H - Hh (FP32)
+    float Hh[9], Hl[9];
     int ncell[3];
     int win[3];       // window half-width (cells) covering the list radius
     int img[3];       // image range, 0 along open axes

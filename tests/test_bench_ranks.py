@@ -66,18 +66,30 @@ def test_reference_arm_other_ranks_exit_quietly(monkeypatch):
 
 
 def test_recorded_traffic_tracks_source(tmp_path, monkeypatch):
+    """The recorded DRAM traffic of a kernel is used only while the kernel's own
+    definition and the pair helpers it inlines are unchanged."""
     sys.path.insert(0, ROOT)
     import bench
-    import hashlib
     import json
     src = tmp_path / "k.cu"
-    src.write_text("kernel v1")
+    other = "__global__ void other(int x) {\n    x += 1;\n}\n"
+    kern = "__global__ void __launch_bounds__(128) k(int x) {\n    x += 2;\n}\n"
+    src.write_text(other + kern)
+    helpers = tmp_path / bench.PAIR_HELPERS
+    helpers.parent.mkdir(parents=True)
+    helpers.write_text("// helpers v1\n")
     (tmp_path / "profiles").mkdir()
-    rec = {"k": {"dram_bytes_per_launch": 123.0, "source": "k.cu",
-                 "sha256": hashlib.sha256(b"kernel v1").hexdigest()}}
-    (tmp_path / "profiles" / "traffic.json").write_text(json.dumps(rec))
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    rec = {"k": {"dram_bytes_per_launch": 123.0, "source": "k.cu",
+                 "kernel_sha256": bench.kernel_source_sha(str(src), "k")}}
+    (tmp_path / "profiles" / "traffic.json").write_text(json.dumps(rec))
     assert bench.recorded_traffic("k") == 123.0
-    src.write_text("kernel v2")
+    src.write_text(other.replace("x += 1", "x += 3") + kern)  # another kernel changed: still valid
+    assert bench.recorded_traffic("k") == 123.0
+    src.write_text(other + kern.replace("x += 2", "x += 4"))  # the kernel changed
+    assert bench.recorded_traffic("k") is None
+    src.write_text(other + kern)
+    assert bench.recorded_traffic("k") == 123.0
+    helpers.write_text("// helpers v2\n")  # an inlined helper changed
     assert bench.recorded_traffic("k") is None
     assert bench.recorded_traffic("other") is None

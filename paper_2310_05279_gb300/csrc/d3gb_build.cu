@@ -45,6 +45,25 @@ __device__ __forceinline__ bool finite_bits(double x) {
     return (__double_as_longlong(x) & 0x7ff0000000000000LL) != 0x7ff0000000000000LL;
 }
 
+// x += n0 H_0 + n1 H_1 + n2 H_2 (lattice rows, bohr).  Translations are nearly
+// always 0 or +-1 per axis, so those cost one FP64 add per component.
+__device__ __forceinline__ void add_lattice(double (&x)[3], const StructGeo& G, int n0, int n1, int n2) {
+    const int n[3] = {n0, n1, n2};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        if (n[k] == 0) continue;
+        const double* Hk = G.H + 3 * k;
+        if (n[k] == 1) {
+            x[0] += Hk[0]; x[1] += Hk[1]; x[2] += Hk[2];
+        } else if (n[k] == -1) {
+            x[0] -= Hk[0]; x[1] -= Hk[1]; x[2] -= Hk[2];
+        } else {
+            const double d = n[k];
+            x[0] += d * Hk[0]; x[1] += d * Hk[1]; x[2] += d * Hk[2];
+        }
+    }
+}
+
 // Wrap into the cell, bin, and record each structure's occupied fractional
 // range per periodic axis (as float bits: the fractions are >= 0).  The
 // lattice translation that wraps an atom is chosen from its FP32 fractional
@@ -86,15 +105,12 @@ __global__ void __launch_bounds__(256) k_wrap(Work w, const double* __restrict__
         w.fw[3 * i + k] = f[k];
     }
     double xw[3] = {xb[0], xb[1], xb[2]};
-    if (n[0] | n[1] | n[2]) {
-        const double n0 = n[0], n1 = n[1], n2 = n[2];
+    if (n[0] | n[1] | n[2]) add_lattice(xw, G, -n[0], -n[1], -n[2]);
 #pragma unroll
-        for (int a = 0; a < 3; ++a) xw[a] = xb[a] - (n0 * G.H[a] + n1 * G.H[3 + a] + n2 * G.H[6 + a]);
-    }
+    for (int a = 0; a < 3; ++a) w.xw[3 * i + a] = xw[a];
+    if (w.skin_half2 > 0.0) {  // references for list reuse
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        w.xw[3 * i + a] = xw[a];
-        if (w.skin_half2 > 0.0) {  // references for list reuse
+        for (int a = 0; a < 3; ++a) {
             w.xref[3 * i + a] = xb[a];
             w.wshift[3 * i + a] = xw[a] - xb[a];
         }
@@ -467,10 +483,8 @@ __global__ void k_fill_ghost(Work w, const int32_t* __restrict__ types, const do
     if (t < 0 || t >= w.T) t = 0;
     const int ps = w.slot_of[i];  // the source's sorted slot (written by k_fill_real)
     const double rk = rk_tab[t];
-    const double d0 = n0, d1 = n1, d2 = n2;
-    double x[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) x[a] = w.xw[3 * i + a] + (d0 * G.H[a] + d1 * G.H[3 + a] + d2 * G.H[6 + a]);
+    double x[3] = {w.xw[3 * i], w.xw[3 * i + 1], w.xw[3 * i + 2]};
+    add_lattice(x, G, n0, n1, n2);
     w.pos64[w.Nr + q] = dbl4_make(x[0], x[1], x[2], rk);
     const float4 hs = w.rec[2 * ps], ls = w.rec[2 * ps + 1];
     const float f0 = (float)n0, f1 = (float)n1, f2 = (float)n2;

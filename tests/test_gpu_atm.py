@@ -51,7 +51,7 @@ def tiny_cells():
     structs = [
         (np.array([[0.3, 0.2, 0.1]]), np.array([1], np.int32), np.diag([3.1, 3.3, 3.7]), np.ones(3, np.int32)),
         (g.uniform(0, 4, (5, 3)), g.integers(0, 3, 5).astype(np.int32),
-         np.array([[4.0, 0, 0], [1.1, 3.9, 0], [-0.6, 0.8, 4.3]]), np.ones(3, np.int32)),
+         np.array([[4.05, 0, 0], [1.1, 3.9, 0], [-0.6, 0.8, 4.3]]), np.ones(3, np.int32)),
         (g.uniform(0, 9, (12, 3)), g.integers(0, 3, 12).astype(np.int32), np.eye(3) * 9.0,
          np.array([1, 1, 0], np.int32)),
         (g.uniform(0, 6, (7, 3)), g.integers(0, 3, 7).astype(np.int32), np.eye(3) * 6.0, np.zeros(3, np.int32)),

@@ -43,7 +43,9 @@ def test_empty_structures_and_small_cells(torch_cuda, oracle_mod, precision):
         (np.zeros((0, 3)), np.zeros(0, np.int32), np.eye(3) * 10.0, np.ones(3, np.int32)),      # no atoms
         (np.array([[0.3, 0.2, 0.1]]), np.array([1], np.int32), np.diag([3.1, 3.3, 3.7]), np.ones(3, np.int32)),
         (g.uniform(0, 4, (5, 3)), g.integers(0, 3, 5).astype(np.int32),
-         np.array([[4.0, 0, 0], [1.1, 3.9, 0], [-0.6, 0.8, 4.3]]), np.ones(3, np.int32)),  # triclinic, tiny
+         np.array([[4.05, 0, 0], [1.1, 3.9, 0], [-0.6, 0.8, 4.3]]), np.ones(3, np.int32)),  # triclinic, tiny
+        # (an edge of 4.0 A would put the image at 3 a1 exactly on R_pot = 12 A, where
+        #  rounding alone decides r < R_pot; every distance here is 4e-5 away from a cutoff)
         (np.zeros((0, 3)), np.zeros(0, np.int32), np.eye(3) * 7.0, np.ones(3, np.int32)),       # no atoms
         (g.uniform(0, 9, (12, 3)), g.integers(0, 3, 12).astype(np.int32), np.eye(3) * 9.0,
          np.array([1, 1, 0], np.int32)),                                                          # slab

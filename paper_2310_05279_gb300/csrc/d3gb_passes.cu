@@ -26,6 +26,23 @@ namespace d3gb {
 
 namespace {
 
+// Running sums of the dispersion pass: a compensated float pair in the mixed
+// form (FP64 runs at 1/64 of the FP32 rate on GB300, and FP64 chunk sums cost
+// the pass about 5%), FP64 in the FP64 form.
+template <bool MIXED> struct PassAcc;
+template <> struct PassAcc<true> {
+    float h = 0.f, l = 0.f;
+    __device__ void add(float x) { acc_add(h, l, x); }
+    __device__ double value() const { return (double)h + (double)l; }
+    __device__ float total() const { return h + l; }
+};
+template <> struct PassAcc<false> {
+    double h = 0.0;
+    __device__ void add(double x) { h += x; }
+    __device__ double value() const { return h; }
+    __device__ double total() const { return h; }
+};
+
 // Eq. 4 counting function f(r) and, optionally, df/dr, in FP64; r from 1/r.
 // (The mixed form evaluates it in double-single, cn_ds below.)
 __device__ __forceinline__ void cn_fun(double rinv, double rc_eff, double, double k1, double& f, double* dfdr) {
@@ -394,8 +411,7 @@ __global__ void __launch_bounds__(128) k_disp(Work w, Consts c, const typename R
     const T rc2 = (T)c.rc_disp2;
     T fx = 0, fy = 0, fz = 0;
     T dnh = 0, dnl = 0;  // dE/dn_i, compensated (it scales the chain-rule forces)
-    double E = 0, Sxx = 0, Syy = 0, Szz = 0, Sxy = 0, Sxz = 0, Syz = 0;
-    double Px = 0, Py = 0, Pz = 0;
+    PassAcc<MIXED> E, Sxx, Syy, Szz, Sxy, Sxz, Syz, Px, Py, Pz;
     for (int k0 = 0; k0 < cnt; k0 += kChunk) {
         const int k1e = min(cnt, k0 + kChunk);
         T e = 0, sxx = 0, syy = 0, szz = 0, sxy = 0, sxz = 0, syz = 0;
@@ -433,18 +449,20 @@ __global__ void __launch_bounds__(128) k_disp(Work w, Consts c, const typename R
             sxx = fma(tx, dx, sxx); syy = fma(ty, dy, syy); szz = fma(tz, dz, szz);
             sxy = fma(tx, dy, sxy); sxz = fma(tx, dz, sxz); syz = fma(ty, dz, syz);
         });
-        E += (double)e;
-        Sxx += (double)sxx; Syy += (double)syy; Szz += (double)szz;
-        Sxy += (double)sxy; Sxz += (double)sxz; Syz += (double)syz;
-        Px += (double)px; Py += (double)py; Pz += (double)pz;
+        E.add(e);
+        Sxx.add(sxx); Syy.add(syy); Szz.add(szz);
+        Sxy.add(sxy); Sxz.add(sxz); Syz.add(syz);
+        if constexpr (ATOMV) {
+            Px.add(px); Py.add(py); Pz.add(pz);
+        }
     }
-    if constexpr (ATOMV) ((T4*)w.Pv)[p] = T4{(T)Px, (T)Py, (T)Pz, (T)0};
-    ((T*)w.dEdn)[p] = (T)((double)dnh + (double)dnl);
+    if constexpr (ATOMV) ((T4*)w.Pv)[p] = T4{(T)Px.total(), (T)Py.total(), (T)Pz.total(), (T)0};
+    ((T*)w.dEdn)[p] = dnh + dnl;
     ((T4*)w.Fd)[p] = T4{fx, fy, fz, (T)0};
-    w.eat[p] = 0.5 * E;
+    w.eat[p] = 0.5 * E.value();
     double* wv = w.wv + 6 * p;
-    wv[0] = -0.5 * Sxx; wv[1] = -0.5 * Syy; wv[2] = -0.5 * Szz;
-    wv[3] = -0.5 * Sxy; wv[4] = -0.5 * Sxz; wv[5] = -0.5 * Syz;
+    wv[0] = -0.5 * Sxx.value(); wv[1] = -0.5 * Syy.value(); wv[2] = -0.5 * Szz.value();
+    wv[3] = -0.5 * Sxy.value(); wv[4] = -0.5 * Sxz.value(); wv[5] = -0.5 * Syz.value();
 }
 
 // ------------------------------------------------------------------ CN chain rule

@@ -17,9 +17,10 @@
 //   k_fin_*           per-structure energy and virial (fixed-order sums)
 //
 // MIXED = true: pair arithmetic in FP32 on split (hi + lo) positions, partial
-// sums promoted to FP64 every kChunk pairs; cutoff tests that fall within the
-// FP32 error band of the cutoff are decided in FP64, so the set of pairs is
-// the FP64 one.  MIXED = false: FP64 throughout.
+// sums of kChunk pairs added into compensated float pairs (dispersion pass) or
+// FP64 sums (chain pass); cutoff tests that fall within the FP32 error band of
+// the cutoff are decided in FP64, so the set of pairs is the FP64 one.
+// MIXED = false: FP64 throughout.
 #include "d3gb_pair.cuh"
 
 namespace d3gb {

@@ -24,8 +24,9 @@ cudaError_t launch_build_impl(const Work& w, const double* pos, const int32_t* t
                               int* bsum, cudaStream_t st);
 int64_t scan_scratch_ints(int64_t ncells);
 cudaError_t launch_backward(const Work& w, const Consts& c, const double* c6d, const dbl4* paird,
-                            const double* cnref, const int* nref, const double* dLdE, const double* dLdF,
-                            double* dLdp, double* dLdx, double* scratch, int B, bool mixed, cudaStream_t st);
+                            const double* cnref, const int* nref, const Tabs& tbm, const double* dLdE,
+                            const double* dLdF, double* dLdp, double* dLdx, double* scratch, int B, bool mixed,
+                            cudaStream_t st);
 int64_t backward_scratch_doubles(const Work& w, int B);
 }  // namespace d3gb
 
@@ -943,7 +944,14 @@ d3_status d3_backward(d3_handle* h, int32_t B, const int64_t* offsets, const dou
         P.bwd_scratch_n = need;
     }
     Consts c = make_consts(h);
-    cudaError_t e = launch_backward(P.w, c, h->d_c6d, h->d_pairb, h->d_cnref, h->d_nref, dLdE, dLdF, dLdparams,
+    Tabs tbm{};  // FP32 tables of the mixed form
+    tbm.c6 = h->d_c6f;
+    tbm.nref = h->d_nref;
+    tbm.rcpair = h->d_rcpair;
+    tbm.exptab = h->d_exptab;
+    tbm.cnref2 = h->d_cnref2;
+    tbm.dcr = h->d_dcr;
+    cudaError_t e = launch_backward(P.w, c, h->d_c6d, h->d_pairb, h->d_cnref, h->d_nref, tbm, dLdE, dLdF, dLdparams,
                                     dLdpos, P.bwd_scratch, B, h->prm.precision == D3_MIXED, st);
     if (e != cudaSuccess) return cuda_fail(h, e, "backward launch");
     return D3_OK;

@@ -1,7 +1,10 @@
 // d3gb_backward.cu -- hand-written backward of (E, F) for damping refits.
-// The handle's precision selects the dispersion pass of the backward: FP64
-// dual numbers, or (mixed form) FP32 dual numbers on split positions with FP64
-// partial sums; the CN, weight and chain passes are FP64 in both.
+// The handle's precision selects the form of the backward: FP64 dual numbers
+// throughout, or (mixed form) the forward's mixed arithmetic for the values --
+// the double-single Eq. 4 term and chain coefficient, float-float Eq. 3
+// exponents, FP32 pair math on split positions -- with FP32 tangents.  GB300
+// runs FP64 at 1/64 of the FP32 rate, so the FP64 passes bound the mixed form's
+// time otherwise.
 //
 // For a loss L(E, F) with upstream gradients gE = dL/dE (per structure) and
 // gF = dL/dF (per atom):
@@ -14,7 +17,7 @@
 // and the coordination-number chain rule) once in dual numbers (value,
 // derivative along u), in FP64.  The coordination numbers are recomputed and
 // nothing is stored per pair.
-#include "d3gb_internal.cuh"
+#include "d3gb_pair.cuh"
 
 namespace d3gb {
 
@@ -410,6 +413,181 @@ __global__ void kb_chain(Work w, BW b, BConsts c, const double* __restrict__ gE,
     }
 }
 
+// ---- mixed form of the CN, weight and chain passes of the backward
+// n (value) as in the forward's CN pass: double-single Eq. 4 term, integer
+// count plus compensated complements; dn/dt = sum_q f'(r)/r (d . u), FP32
+// (compensated), u the tangent of d.
+__global__ void __launch_bounds__(128) kb_cn_mixed(Work w, BW b, Consts c, const float4* __restrict__ rcpair,
+                                                   const float2* __restrict__ exptab) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= w.Nr) return;
+    const Site<true> S(w, p);
+    const StructGeo& G = w.geo[w.sid[p]];
+    const ListView LV{w.nbr_cn + list_row(G.list_base_cn, p - G.atom_base, G.cap_cn)};
+    const int cnt = w.cnt_cn[p];
+    const float4* rrow = rcpair + (S.tsrc() & 15) * c.T;
+    const float k1 = c.k1f, rc2 = c.rc_cn2f;
+    const float4 tp = b.xdf[p];
+    float nh = 0.f, nl = 0.f, th = 0.f, tl = 0.f;
+    int nint = 0;
+    LV.for_each(0, cnt, [&](int q) {
+        float D[3], r2, ah, al, rch;
+        int tq;
+        if (!cn_pair_precise(S, q, rrow, k1, rc2, c.rc_cn2, D, r2, ah, al, rch, tq)) return;
+        const CnDS z = cn_ds(ah, al, exptab);
+        if (z.th < 1.0f) {
+            ++nint;
+            acc_add(nh, nl, -z.ch);
+            nl -= z.cl;
+        } else {
+            acc_add(nh, nl, z.fh);
+            nl += z.fl;
+        }
+        const float4 uq = b.xdf[q];
+        const float du = fmaf(D[0], uq.x - tp.x, fmaf(D[1], uq.y - tp.y, D[2] * (uq.z - tp.z)));
+        const float ri = rsqrt_nr(r2);
+        acc_add(th, tl, -k1 * rch * z.fh * z.ch * (ri * ri * ri) * du);
+    });
+    b.n[p] = Dual{(double)nint + (double)nh + (double)nl, (double)th + (double)tl};
+}
+
+// Weights (Eq. 3) as dual numbers: values with float-float exponents as in the
+// forward, tangents in FP32; dW/dn = -2 k3 W_a sum_b W_b (nref_b - nref_a) from
+// the table of reference differences (no cancellation against n).  The shift
+// by the largest exponent is a constant: it cancels in the normalisation.
+template <int R>
+__global__ void __launch_bounds__(128) kb_weights_mixed(Work w, BW b, Consts c, const float2* __restrict__ cnref2,
+                                                        const float* __restrict__ dcr, const int* __restrict__ nref,
+                                                        const float* __restrict__ c6) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= w.Nr) return;
+    const int t = rec_tsrc(w, p) & 15;
+    const Dual nd = b.n[p];
+    const float Nh = (float)nd.v, Nl = (float)(nd.v - (double)Nh), nt = (float)nd.t;
+    const int nr = nref[t];
+    float xh[R], xl[R], xt[R];
+    float mh = -3.0e38f, ml = 0.0f;
+#pragma unroll
+    for (int a = 0; a < R; ++a) {
+        const float2 cr = cnref2[t * R + a];
+        float zh, ze, zl;
+        two_sum(Nh, -cr.x, zh, ze);
+        two_sum(zh, ze + (Nl - cr.y), zh, zl);
+        const float ph = zh * zh, pl = fmaf(zh, zh, -ph) + 2.0f * zh * zl;
+        xh[a] = -c.k3h * ph;
+        xl[a] = fmaf(-c.k3h, ph, -xh[a]) - c.k3h * pl - c.k3l * ph;
+        xt[a] = -2.0f * c.k3f * zh * nt;
+        if (a < nr && (xh[a] > mh || (xh[a] == mh && xl[a] > ml))) {
+            mh = xh[a];
+            ml = xl[a];
+        }
+    }
+    DF L[R];
+    DF sum = DF{0.f, 0.f};
+#pragma unroll
+    for (int a = 0; a < R; ++a) {
+        L[a] = DF{0.f, 0.f};
+        if (a < nr) {
+            float yh, ye, yl;
+            two_sum(xh[a], -mh, yh, ye);
+            two_sum(yh, ye + (xl[a] - ml), yh, yl);
+            const float e = expf(yh) * (1.0f + yl);
+            L[a] = DF{e, e * xt[a]};
+        }
+        sum = sum + L[a];
+    }
+    const DF is = finv(sum);
+#pragma unroll
+    for (int a = 0; a < R; ++a) L[a] = L[a] * is;
+#pragma unroll
+    for (int a = 0; a < R; ++a) {
+        DF sa = DF{0.f, 0.f};
+        const float* dr = dcr + (t * R + a) * R;
+#pragma unroll
+        for (int bb = 0; bb < R; ++bb) sa = sa + dr[bb] * L[bb];
+        const DF dW = (-2.0f * c.k3f) * (L[a] * sa);
+        b.W[p * R + a] = Dual{(double)L[a].v, (double)L[a].t};
+        b.dW[p * R + a] = Dual{(double)dW.v, (double)dW.t};
+    }
+    // v rows (values then tangents, each padded to RP = 4 or 8) as whole 16-byte stores
+    constexpr int RP = R <= 4 ? 4 : 8;
+    for (int u = 0; u < c.T; ++u) {
+        const float* cu = c6 + ((size_t)(u * c.T + t) * R) * R;  // C6ref[u][t][a][b]
+        float vv[RP], vt[RP];
+#pragma unroll
+        for (int a = 0; a < RP; ++a) {
+            DF sv = DF{0.f, 0.f};
+            if (a < R) {
+#pragma unroll
+                for (int bb = 0; bb < R; ++bb) sv = sv + cu[a * R + bb] * L[bb];
+            }
+            vv[a] = sv.v;
+            vt[a] = sv.t;
+        }
+        float4* dst = reinterpret_cast<float4*>(b.vf + (p * c.T + u) * 2 * RP);
+#pragma unroll
+        for (int k = 0; k < RP / 4; ++k) {
+            dst[k] = make_float4(vv[4 * k], vv[4 * k + 1], vv[4 * k + 2], vv[4 * k + 3]);
+            dst[RP / 4 + k] = make_float4(vt[4 * k], vt[4 * k + 1], vt[4 * k + 2], vt[4 * k + 3]);
+        }
+    }
+}
+
+// Chain rule as dual numbers: the value of the coefficient f'(r)/r as in the
+// forward's chain pass (double-single, rounded once), its tangent
+// d(f'/r)/dt = -k1 rc [(1 - 2f) f' / r^3 - 3 f (1 - f) / r^4] (d . u) / r in FP32.
+__global__ void __launch_bounds__(128) kb_chain_mixed(Work w, BW b, Consts c, const float4* __restrict__ rcpair,
+                                                      const float2* __restrict__ exptab,
+                                                      const double* __restrict__ gE, double* __restrict__ dLdx) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= w.Nr) return;
+    const Site<true> S(w, p);
+    const int s = w.sid[p];
+    const StructGeo& G = w.geo[s];
+    const ListView LV{w.nbr_cn + list_row(G.list_base_cn, p - G.atom_base, G.cap_cn)};
+    const int cnt = w.cnt_cn[p];
+    const float4* rrow = rcpair + (S.tsrc() & 15) * c.T;
+    const float k1 = c.k1f, rc2 = c.rc_cn2f;
+    const Dual dnd = b.dEdn[p];
+    const float dni = (float)dnd.v, dnit = (float)dnd.t;
+    const float4 tp = b.xdf[p];
+    float fv[3] = {0.f, 0.f, 0.f}, ft[3] = {0.f, 0.f, 0.f};
+    LV.for_each(0, cnt, [&](int q) {
+        float D[3], r2, ah, al, rch, rcl, r2l;
+        int tq;
+        if (!cn_pair_precise(S, q, rrow, k1, rc2, c.rc_cn2, D, r2, ah, al, rch, tq, &rcl, &r2l)) return;
+        const CnDS z = cn_ds(ah, al, exptab);
+        const float g = chain_coef(z, r2, r2l, rch, rcl, k1);
+        const Dual dqd = b.dEdn[tq >> 4];
+        const float dnq = (float)dqd.v, dnqt = (float)dqd.t;
+        const float4 uq = b.xdf[q];
+        const float u[3] = {uq.x - tp.x, uq.y - tp.y, uq.z - tp.z};
+        const float du = fmaf(D[0], u[0], fmaf(D[1], u[1], D[2] * u[2]));
+        const float ri = rsqrt_nr(r2), ri2 = ri * ri;
+        const float f = z.fh, omf = z.ch;  // f and 1 - f
+        const float fp = -k1 * rch * f * omf * ri2;  // f'(r)
+        const float dgdr = -k1 * rch * ((1.0f - 2.0f * f) * fp * ri2 * ri - 3.0f * f * omf * ri2 * ri2);
+        const float gt = dgdr * du * ri;
+        const float cv = (dni + dnq) * g;
+        const float ct = fmaf(dnit + dnqt, g, (dni + dnq) * gt);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            fv[a] = fmaf(cv, D[a], fv[a]);
+            ft[a] = fmaf(ct, D[a], fmaf(cv, u[a], ft[a]));
+        }
+    });
+    if (dLdx) {
+        const double uc = kHartreeEV / kBohrA;
+        const double ge = gE[s];
+        const int i = w.perm[p];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const Dual Fd = b.F[3 * p + a];
+            dLdx[3 * (int64_t)i + a] = (-ge * (Fd.v + (double)fv[a]) + (Fd.t + (double)ft[a])) * uc;
+        }
+    }
+}
+
 // per-structure sums of dE/dtheta (value and tangent), fixed order
 __global__ void __launch_bounds__(256) kb_struct_sum(Work w, BW b) {
     const int s = blockIdx.x;
@@ -460,21 +638,26 @@ inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
 template <int R>
 cudaError_t backward_impl(const Work& w, const Consts& cc, const double* c6d, const dbl4* pairb, const double* cnref,
-                          const int* nref, const double* gE, const double* gF, double* dLdp, double* dLdx,
-                          double* scratch, int B, bool mixed, cudaStream_t st) {
+                          const int* nref, const Tabs& tbm, const double* gE, const double* gF, double* dLdp,
+                          double* dLdx, double* scratch, int B, bool mixed, cudaStream_t st) {
     BW b = carve(scratch, w.Nr, w.ghost_cap, w.T, R, B);
     BConsts c{cc.rc_disp2, cc.rc_cn2, cc.k1, cc.k3, cc.s6, cc.s8, cc.T, R};
     const int TB = 128;
     if (w.Nr > 0) {
         // tangent positions for real atoms and every image actually built
         kb_xdot<<<nblk(w.Nr + w.ghost_cap, TB), TB, 0, st>>>(w, b, gF, w.Nr + w.ghost_cap);
-        kb_cn<<<nblk(w.Nr, TB), TB, 0, st>>>(w, b, c);
-        kb_weights<R><<<nblk(w.Nr, TB), TB, 0, st>>>(w, b, c, cnref, nref, c6d);
-        if (mixed)
+        if (mixed) {
+            kb_cn_mixed<<<nblk(w.Nr, TB), TB, 0, st>>>(w, b, cc, tbm.rcpair, tbm.exptab);
+            kb_weights_mixed<R><<<nblk(w.Nr, TB), TB, 0, st>>>(w, b, cc, tbm.cnref2, tbm.dcr, tbm.nref,
+                                                                (const float*)tbm.c6);
             kb_disp_mixed<R><<<nblk(w.Nr, TB), TB, 0, st>>>(w, b, c, pairb);
-        else
+            kb_chain_mixed<<<nblk(w.Nr, TB), TB, 0, st>>>(w, b, cc, tbm.rcpair, tbm.exptab, gE, dLdx);
+        } else {
+            kb_cn<<<nblk(w.Nr, TB), TB, 0, st>>>(w, b, c);
+            kb_weights<R><<<nblk(w.Nr, TB), TB, 0, st>>>(w, b, c, cnref, nref, c6d);
             kb_disp<R><<<nblk(w.Nr, TB), TB, 0, st>>>(w, b, c, pairb);
-        kb_chain<<<nblk(w.Nr, TB), TB, 0, st>>>(w, b, c, gE, dLdx);
+            kb_chain<<<nblk(w.Nr, TB), TB, 0, st>>>(w, b, c, gE, dLdx);
+        }
     }
     kb_struct_sum<<<B, 256, 0, st>>>(w, b);
     if (dLdp) kb_param_grad<<<1, 256, 0, st>>>(b, B, gE, dLdp);
@@ -492,10 +675,11 @@ int64_t backward_scratch_doubles(const Work& w, int B) {
 }
 
 cudaError_t launch_backward(const Work& w, const Consts& c, const double* c6d, const dbl4* pairb,
-                            const double* cnref, const int* nref, const double* dLdE, const double* dLdF,
-                            double* dLdp, double* dLdx, double* scratch, int B, bool mixed, cudaStream_t st) {
+                            const double* cnref, const int* nref, const Tabs& tbm, const double* dLdE,
+                            const double* dLdF, double* dLdp, double* dLdx, double* scratch, int B, bool mixed,
+                            cudaStream_t st) {
 #define D3_BWD(RR) \
-    return backward_impl<RR>(w, c, c6d, pairb, cnref, nref, dLdE, dLdF, dLdp, dLdx, scratch, B, mixed, st)
+    return backward_impl<RR>(w, c, c6d, pairb, cnref, nref, tbm, dLdE, dLdF, dLdp, dLdx, scratch, B, mixed, st)
     switch (c.R) {
         case 1: D3_BWD(1);
         case 2: D3_BWD(2);

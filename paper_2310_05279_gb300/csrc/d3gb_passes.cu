@@ -55,125 +55,6 @@ __device__ __forceinline__ double inv_sqrt(double x) { return 1.0 / sqrt(x); }
 __device__ __forceinline__ float recip(float x) { return rcp_approx(x); }
 __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 
-// Mixed form: pair vector D (FP32), r^2 and the Eq. 4 exponent a = k1 (rc/r - 1)
-// as a double-single pair (ah + al) from the exact pair vector D + e:
-//   r^2 = Sh + Sl (TwoProd/TwoSum), u = rc^2 - r^2, r = sqrt(r^2) with its
-//   correction term, den = r^2 + r rc, a = k1 u / den with one residual step.
-// Its error is a few units of 2^-48 relative, so exp(-a) is as accurate as
-// expf itself.  Returns false when the pair is outside R_cn.
-__device__ __forceinline__ bool cn_pair_precise(const Site<true>& S, int q, const float4* rrow, float k1, float rc2,
-                                                double rc2d, float (&D)[3], float& r2, float& ah, float& al,
-                                                float& rch, int& tq, float* rcl_out = nullptr,
-                                                float* r2l_out = nullptr) {
-    float e[3];
-    S.dist_exact(q, D, e, tq);
-    float P[3], pl[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        P[k] = D[k] * D[k];
-        pl[k] = fmaf(D[k], D[k], -P[k]);
-    }
-    float S1, s1, Sh, s2;
-    two_sum(P[0], P[1], S1, s1);
-    two_sum(S1, P[2], Sh, s2);
-    float Sl = (s1 + s2) + (pl[0] + pl[1] + pl[2]) + 2.0f * (D[0] * e[0] + D[1] * e[1] + D[2] * e[2]);
-    two_sum(Sh, Sl, Sh, Sl);  // normalise
-    r2 = Sh;
-    if (!S.inside(q, r2, rc2, rc2d)) return false;
-    const float4 rc = rrow[tq & 15];  // rc hi, rc lo, rc^2 hi, rc^2 lo
-    float uh, ue;
-    two_sum(rc.z, -Sh, uh, ue);
-    const float ul = ue + (rc.w - Sl);
-    const float rh = Sh * rsqrt_nr(Sh);
-    const float rl = (fmaf(-rh, rh, Sh) + Sl) * (0.5f / rh);
-    const float ph = rh * rc.x, pe = fmaf(rh, rc.x, -ph);
-    float dh, de;
-    two_sum(Sh, ph, dh, de);
-    const float dl = de + Sl + pe + rh * rc.y + rl * rc.x;
-    const float idh = rcp_nr(dh);
-    const float qh = uh * idh;
-    const float ql = (fmaf(-qh, dh, uh) + ul - qh * dl) * idh;
-    ah = k1 * qh;
-    al = fmaf(k1, qh, -ah) + k1 * ql;
-    rch = rc.x;
-    if (rcl_out) *rcl_out = rc.y;
-    if (r2l_out) *r2l_out = Sl;
-    return true;
-}
-
-// ------------------------------------------------------------------ Eq. 4 in double-single
-// t = exp(-a), f = 1/(1 + t) and 1 - f = t f for a = ah + al, each as a
-// double-single pair with a relative error near 1e-11.  The coordination number
-// and its chain-rule forces are sums of many such terms; FP32 rounding of each
-// would leave a small systematic error that the sums accumulate, so the terms
-// are formed here from FP32 operations with error-free transformations.
-//
-// exp follows the table-driven method of P. T. P. Tang (ACM TOMS 15(2), 1989):
-// x = (64 m + j) L + r with L = ln2/64 (carried in three FP32 parts so that the
-// reduction is exact to ~1e-14), exp(x) = 2^m 2^(j/64) exp(r), |r| <= L/2, and
-// exp(r) = 1 + r + r^2/2 + r^3/6 + r^4/24 (truncation below 4e-14).  The table
-// holds 2^(j/64) as FP32 hi + lo pairs.
-constexpr double kLnTwoOver64 = 0.693147180559945309417232121458 / 64.0;
-constexpr float kExpL1 = 1420.0f / 131072.0f;  // 11 significant bits: k L1 is exact for |k| < 2^13
-constexpr float kExpL2 = (float)(kLnTwoOver64 - (double)kExpL1);
-constexpr float kExpL3 = (float)((kLnTwoOver64 - (double)kExpL1) - (double)kExpL2);
-constexpr float kExpInvL = (float)(64.0 / 0.693147180559945309417232121458);
-
-struct CnDS {
-    float th, tl;  // t = exp(-a)
-    float fh, fl;  // f = 1 / (1 + t)
-    float ch, cl;  // 1 - f = t f
-};
-
-__device__ __forceinline__ CnDS cn_ds(float ah, float al, const float2* __restrict__ tab) {
-    // x = -a, clamped so that 2^m stays a normal FP32 scale (|x| <= 87: t in [1.6e-38, 6e37])
-    float xh = -ah, xl = -al;
-    if (fabsf(xh) > 87.0f) { xh = copysignf(87.0f, xh); xl = 0.0f; }
-    const float kf = rintf(xh * kExpInvL);
-    const int k = (int)kf;
-    const float r1 = fmaf(-kf, kExpL1, xh);  // exact (see kExpL1)
-    const float p2 = kf * kExpL2, p2e = fmaf(kf, kExpL2, -p2);
-    float rh, re;
-    two_sum(r1, -p2, rh, re);
-    const float rl = ((re - p2e) - kf * kExpL3) + xl;
-    // exp(r) - 1 = rh + s
-    const float s = rl + rh * rl + rh * rh * fmaf(rh, fmaf(rh, 1.0f / 24.0f, 1.0f / 6.0f), 0.5f);
-    const int j = k & 63, m = (k - j) / 64;
-    const float2 T = __ldg(tab + j);
-    const float ph = T.x * rh, pe = fmaf(T.x, rh, -ph);
-    const float hh = T.x + ph, he = ph - (hh - T.x);  // |T.x| >= |ph|: Fast2Sum
-    const float lo = he + pe + T.y + fmaf(T.x, s, T.y * rh);
-    float th = hh + lo;
-    float tl = lo - (th - hh);
-    th = ldexpf(th, m);
-    tl = ldexpf(tl, m);
-    CnDS o;
-    o.th = th;
-    o.tl = tl;
-    // f = 1/(1 + t) with one residual correction
-    float dh, de;
-    two_sum(1.0f, th, dh, de);
-    const float dl = de + tl;
-    const float y = rcp_nr(dh);
-    const float rho = fmaf(-dh, y, 1.0f) - dl * y;
-    o.fh = y;
-    o.fl = y * rho;
-    // 1 - f = t f
-    const float ch = th * o.fh;
-    o.ch = ch;
-    o.cl = fmaf(th, o.fh, -ch) + fmaf(th, o.fl, tl * o.fh);
-    return o;
-}
-
-// double-single product (ah + al)(bh + bl), result as hi + lo
-__device__ __forceinline__ void ds_mul(float ah, float al, float bh, float bl, float& h, float& l) {
-    const float p = ah * bh;
-    const float e = fmaf(ah, bh, -p);
-    l = fmaf(ah, bl, fmaf(al, bh, e));
-    h = p + l;
-    l = l - (h - p);
-}
-
 // ------------------------------------------------------------------ Eq. 3
 // Per atom, right after its coordination number (fused into the CN pass): the
 // exponents -k3 (n - nref_a)^2 minus their maximum are formed in FP64 (their
@@ -513,19 +394,7 @@ __global__ void __launch_bounds__(128) k_chain(Work w, Consts c, const float4* _
                                      &rcl, &r2l))
                     return;
                 const CnDS z = cn_ds(ah, al, exptab);
-                // 1/r from r^2 = r2 + r2l with one residual step (double-single)
-                const float y0 = rsqrt_nr(r2);
-                const float y2 = y0 * y0, y2e = fmaf(y0, y0, -y2);
-                const float ry = fmaf(-r2, y2, 1.0f) - fmaf(r2, y2e, r2l * y2);
-                const float yh = y0, yl = 0.5f * y0 * ry;
-                // f'(r)/r = -k1 rc f (1 - f) / r^3, formed in double-single and rounded once
-                float a2h, a2l, a3h, a3l, cfh, cfl, uh, ul, gh, gl;
-                ds_mul(yh, yl, yh, yl, a2h, a2l);
-                ds_mul(a2h, a2l, yh, yl, a3h, a3l);
-                ds_mul(z.ch, z.cl, z.fh, z.fl, cfh, cfl);
-                ds_mul(rch, rcl, cfh, cfl, uh, ul);
-                ds_mul(uh, ul, a3h, a3l, gh, gl);
-                g = -k1 * (gh + gl);
+                g = chain_coef(z, r2, r2l, rch, rcl, k1);
                 srcq = tq >> 4;
                 dnq = dEdn[srcq];
                 dx = D[0]; dy = D[1]; dz = D[2];

@@ -65,6 +65,7 @@ struct BW {
     // mixed form of the dispersion pass
     float* vf;    // [Nr][T][2 * RP]: R values of v padded to RP, then R tangents padded to RP
     float4* xdf;  // [Nr + ghost_cap] tangent positions as FP32
+    float2* dEdnf;  // [Nr] dE/dn (value, tangent) as FP32 for the chain pass
     int RP;
 };
 
@@ -95,6 +96,8 @@ __host__ __device__ inline BW carve(double* s, int64_t Nr, int64_t Ng, int T, in
     b.vf = reinterpret_cast<float*>(x);
     x += Nr * T * b.RP;
     b.xdf = reinterpret_cast<float4*>(x);
+    x += 2 * (Nr + Ng);
+    b.dEdnf = reinterpret_cast<float2*>(x);
     return b;
 }
 
@@ -271,6 +274,12 @@ __device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) 
     const float bb = s - a;
     e = (a - (s - bb)) + (b - bb);
 }
+// compensated float-pair running sum (value h + l)
+struct FF {
+    float h = 0.f, l = 0.f;
+    __device__ void add(float x) { acc_add(h, l, x); }
+    __device__ double value() const { return (double)h + (double)l; }
+};
 
 template <int R>
 __global__ void __launch_bounds__(128) kb_disp_mixed(Work w, BW b, BConsts c, const dbl4* __restrict__ pairb) {
@@ -306,9 +315,11 @@ __global__ void __launch_bounds__(128) kb_disp_mixed(Work w, BW b, BConsts c, co
     const ListView LV{w.nbr_disp + list_row(G.list_base_disp, p - G.atom_base, G.cap_disp)};
     const int cnt = w.cnt_disp[p];
     const float rc2f = (float)c.rc_disp2, s6 = (float)c.s6;
-    const int stride = c.T * 2 * b.RP;
+    constexpr int RP = R <= 4 ? 4 : 8;  // b.RP
+    const int stride = c.T * 2 * RP;
     float dnh = 0.0f, dnl = 0.0f;
-    double dnt = 0.0, Fv[3] = {0, 0, 0}, Ft[3] = {0, 0, 0}, thv[4] = {0, 0, 0, 0}, tht[4] = {0, 0, 0, 0};
+    // running sums as compensated float pairs (FP64 runs at 1/64 of the FP32 rate)
+    FF dnt, Fv[3], Ft[3], thv[4], tht[4];
     for (int k0 = 0; k0 < cnt; k0 += kChunk) {
         const int k1e = min(cnt, k0 + kChunk);
         float dt = 0.0f, fv[3] = {0, 0, 0}, ft[3] = {0, 0, 0}, hv[4] = {0, 0, 0, 0}, ht[4] = {0, 0, 0, 0};
@@ -332,11 +343,15 @@ __global__ void __launch_bounds__(128) kb_disp_mixed(Work w, BW b, BConsts c, co
             const float ux = tq.x - tp.x, uy = tq.y - tp.y, uz = tq.z - tp.z;
             const DF r2 = DF{r2v, 2.0f * fmaf(dx, ux, fmaf(dy, uy, dz * uz))};
             const float* tb = tab[ti * c.T + (tsq & 15)];
-            const float* vq = b.vf + (int64_t)(tsq >> 4) * stride + ti * 2 * b.RP;
+            // the v row of q for type t_i: R values, then R tangents, each padded to RP (vector loads)
+            const float* vq = b.vf + (int64_t)(tsq >> 4) * stride + ti * 2 * RP;
+            float vv[R], vt[R];
+            load_vec<R>(vq, vv);
+            load_vec<R>(vq + RP, vt);
             DF C6 = DF{0.0f, 0.0f}, dC6 = DF{0.0f, 0.0f};
 #pragma unroll
             for (int a = 0; a < R; ++a) {
-                const DF v = DF{vq[a], vq[b.RP + a]};
+                const DF v = DF{vv[a], vt[a]};
                 C6 = C6 + Wi[a] * v;
                 dC6 = dC6 + dWi[a] * v;
             }
@@ -361,23 +376,24 @@ __global__ void __launch_bounds__(128) kb_disp_mixed(Work w, BW b, BConsts c, co
             hv[2] = fmaf(tb[3], dR.v, hv[2]); ht[2] = fmaf(tb[3], dR.t, ht[2]);
             hv[3] += dR.v; ht[3] += dR.t;
         });
-        dnt += (double)dt;
+        dnt.add(dt);
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            Fv[a] += (double)fv[a];
-            Ft[a] += (double)ft[a];
+            Fv[a].add(fv[a]);
+            Ft[a].add(ft[a]);
         }
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
-            thv[m] += (double)hv[m];
-            tht[m] += (double)ht[m];
+            thv[m].add(hv[m]);
+            tht[m].add(ht[m]);
         }
     }
-    b.dEdn[p] = Dual{(double)dnh + (double)dnl, dnt};
+    b.dEdn[p] = Dual{(double)dnh + (double)dnl, dnt.value()};
+    b.dEdnf[p] = make_float2(dnh + dnl, dnt.h + dnt.l);
 #pragma unroll
-    for (int a = 0; a < 3; ++a) b.F[3 * p + a] = Dual{Fv[a], Ft[a]};
+    for (int a = 0; a < 3; ++a) b.F[3 * p + a] = Dual{Fv[a].value(), Ft[a].value()};
 #pragma unroll
-    for (int m = 0; m < 4; ++m) b.th[4 * p + m] = Dual{0.5 * thv[m], 0.5 * tht[m]};
+    for (int m = 0; m < 4; ++m) b.th[4 * p + m] = Dual{0.5 * thv[m].value(), 0.5 * tht[m].value()};
 }
 
 __global__ void kb_chain(Work w, BW b, BConsts c, const double* __restrict__ gE, double* __restrict__ dLdx) {
@@ -548,8 +564,8 @@ __global__ void __launch_bounds__(128) kb_chain_mixed(Work w, BW b, Consts c, co
     const int cnt = w.cnt_cn[p];
     const float4* rrow = rcpair + (S.tsrc() & 15) * c.T;
     const float k1 = c.k1f, rc2 = c.rc_cn2f;
-    const Dual dnd = b.dEdn[p];
-    const float dni = (float)dnd.v, dnit = (float)dnd.t;
+    const float2 dnd = b.dEdnf[p];
+    const float dni = dnd.x, dnit = dnd.y;
     const float4 tp = b.xdf[p];
     float fv[3] = {0.f, 0.f, 0.f}, ft[3] = {0.f, 0.f, 0.f};
     LV.for_each(0, cnt, [&](int q) {
@@ -558,8 +574,8 @@ __global__ void __launch_bounds__(128) kb_chain_mixed(Work w, BW b, Consts c, co
         if (!cn_pair_precise(S, q, rrow, k1, rc2, c.rc_cn2, D, r2, ah, al, rch, tq, &rcl, &r2l)) return;
         const CnDS z = cn_ds(ah, al, exptab);
         const float g = chain_coef(z, r2, r2l, rch, rcl, k1);
-        const Dual dqd = b.dEdn[tq >> 4];
-        const float dnq = (float)dqd.v, dnqt = (float)dqd.t;
+        const float2 dqd = b.dEdnf[tq >> 4];
+        const float dnq = dqd.x, dnqt = dqd.y;
         const float4 uq = b.xdf[q];
         const float u[3] = {uq.x - tp.x, uq.y - tp.y, uq.z - tp.z};
         const float du = fmaf(D[0], u[0], fmaf(D[1], u[1], D[2] * u[2]));
@@ -671,7 +687,7 @@ int64_t backward_scratch_doubles(const Work& w, int B) {
     const int64_t duals = Nr * (1 + 2 * (int64_t)w.R + (int64_t)w.T * w.R + 1 + 3 + 4);
     const int64_t rp = w.R <= 4 ? 4 : 8;
     // duals, tangent positions, per-structure sums, FP32 v rows and tangents (+ alignment)
-    return 2 * duals + 3 * (Nr + Ng) + 8 * (int64_t)B + Nr * (int64_t)w.T * rp + 2 * (Nr + Ng) + 64;
+    return 2 * duals + 3 * (Nr + Ng) + 8 * (int64_t)B + Nr * (int64_t)w.T * rp + 2 * (Nr + Ng) + Nr + 64;
 }
 
 cudaError_t launch_backward(const Work& w, const Consts& c, const double* c6d, const dbl4* pairb,

@@ -23,8 +23,8 @@ namespace {
 //
 // One warp per atom i.  The lanes stage i's neighbours within rc3 in shared
 // memory (vector, r^2, C6_ij and its n_i-derivative, W_j), then test the
-// unordered pairs (j, k) of them: lane-strided partners j, each with the n/2
-// slots that follow it cyclically, so every pair is tested once.  Most pairs
+// unordered pairs of them, numbered as (j, j + s mod n) for s = 1 .. n/2 and
+// dealt to the lanes 32 at a time, so every pair is tested once.  Most pairs
 // fail the third side's cutoff, so the pairs that pass are queued in shared
 // memory (ballot compaction) and evaluated 32 at a time with every lane busy.
 // The warp writes only atom i's results; every triangle is visited once from

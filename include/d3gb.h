@@ -28,8 +28,14 @@
  *    geometry allocate nothing and do not synchronise, so they can be captured
  *    in a CUDA graph.
  *  - Errors: every call returns a d3_status.  Device-side problems (capacity
- *    overflow, non-finite coordinates, bad types) are recorded in a status word
- *    that d3_sync_status() reads.  The library never aborts or traps.
+ *    overflow, non-finite coordinates, bad types, coordinates out of range) are
+ *    recorded in a status word that d3_sync_status() reads.  The library never
+ *    aborts or traps.
+ *  - Coordinate range: after wrapping into its cell (periodic axes) every
+ *    position must satisfy |x| < 4200 A (8000 bohr; the FP32 split of positions
+ *    on a 2^-10 bohr grid is exact below 2^13 bohr).  A cell that reaches
+ *    beyond it is rejected with D3_ERR_ARG at the call; a position beyond it is
+ *    reported as D3_ERR_ARG by d3_sync_status().
  *  - Thread safety: one handle must not be used from two host threads at once.
  */
 #ifndef D3GB_H
@@ -205,11 +211,12 @@ d3_status d3_compute_batch_host(d3_handle *h, int32_t B, const int64_t *offsets,
  *   dLdpos     device double[N][3] = dL/dx (per A), input order
  * The force term needs the Hessian-vector product H*(dL/dF); it is formed by
  * forward-mode differentiation of the whole force evaluation along dL/dF
- * (coordination numbers recomputed, no per-pair storage).  The coordination
- * numbers, weights and chain rule are in FP64; the dispersion pair terms are
- * FP64 for a D3_FP64 handle and FP32 dual numbers with FP64 partial sums for
- * a D3_MIXED handle (several times faster, same relative precision as the
- * mixed forward).  Either output may be NULL.  Inputs as in d3_compute_batch. */
+ * (coordination numbers recomputed, no per-pair storage).  A D3_FP64 handle
+ * differentiates in FP64 dual numbers; a D3_MIXED handle forms the values with
+ * the mixed forward's arithmetic (double-single Eq. 4 terms, float-float Eq. 3
+ * exponents, FP32 pair math on split positions, compensated sums) and the
+ * tangents in FP32, several times faster with the mixed forward's relative
+ * precision.  Either output may be NULL.  Inputs as in d3_compute_batch. */
 d3_status d3_backward(d3_handle *h, int32_t B, const int64_t *offsets, const double *pos, const int32_t *types,
                       const double *cells, const int32_t *pbc, const double *dLdE, const double *dLdF,
                       double *dLdparams, double *dLdpos, void *stream);

@@ -238,6 +238,19 @@ d3_status plan_geometry(d3_handle* h, Plan& P, int32_t B, const int64_t* offsets
         if (!(std::fabs(det) > 1e-9 * scale * scale * scale) || !std::isfinite(det))
             return fail(h, D3_ERR_ARG, "degenerate or non-finite cell for structure " + std::to_string(s));
         inv3(G.H, G.Hinv);
+        // the far corner of the cell (where wrapped positions end) must stay in the coordinate range
+        double corner = 0.0;
+        for (int m = 0; m < 8; ++m) {
+            double c2 = 0.0;
+            for (int a = 0; a < 3; ++a) {
+                const double x = ((m & 1) ? G.H[a] : 0.0) + ((m & 2) ? G.H[3 + a] : 0.0) + ((m & 4) ? G.H[6 + a] : 0.0);
+                c2 += x * x;
+            }
+            corner = std::max(corner, std::sqrt(c2));
+        }
+        if (!(corner + rl < (double)kMaxCoordBohr))
+            return fail(h, D3_ERR_ARG, "cell of structure " + std::to_string(s) +
+                                            " extends beyond the supported coordinate range (4200 A)");
         const int64_t n = offsets[s + 1] - offsets[s];
         if (n < 0) return fail(h, D3_ERR_ARG, "offsets must be non-decreasing");
         if (n > (int64_t)1 << 27) return fail(h, D3_ERR_ARG, "structure too large (max 2^27 atoms)");
@@ -967,6 +980,8 @@ d3_status d3_sync_status(d3_handle* h) {
     if (e != cudaSuccess) return cuda_fail(h, e, "status read");
     if (st & ST_NONFINITE) return fail(h, D3_ERR_NONFINITE, "non-finite coordinate");
     if (st & ST_TYPE) return fail(h, D3_ERR_TYPE, "atom type out of range");
+    if (st & ST_RANGE)
+        return fail(h, D3_ERR_ARG, "a coordinate lies beyond the supported range (|x| < 4200 A after wrapping)");
     if (st & (ST_GHOST_CAP | ST_LIST_CAP)) {
         h->plan.sized = false;  // the next call re-measures and regrows
         return fail(h, D3_ERR_CAPACITY, "neighbour or image capacity exceeded; buffers will be regrown");

@@ -106,6 +106,14 @@ __global__ void __launch_bounds__(256) k_wrap(Work w, const double* __restrict__
     }
     double xw[3] = {xb[0], xb[1], xb[2]};
     if (n[0] | n[1] | n[2]) add_lattice(xw, G, -n[0], -n[1], -n[2]);
+    // the exact FP32 split of positions needs |x| < 2^13 bohr (checked in FP32)
+    bool far = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float xr = xf[a] - ((float)n[0] * G.Hh[a] + (float)n[1] * G.Hh[3 + a] + (float)n[2] * G.Hh[6 + a]);
+        far = far || !(fabsf(xr) < kMaxCoordBohr);
+    }
+    if (far && fin) atomicOr(w.status, ST_RANGE);
 #pragma unroll
     for (int a = 0; a < 3; ++a) w.xw[3 * i + a] = xw[a];
     if (w.skin_half2 > 0.0) {  // references for list reuse

@@ -40,7 +40,11 @@ enum StatusBits : int {
     ST_LIST_CAP = 2,
     ST_NONFINITE = 4,
     ST_TYPE = 8,
+    ST_RANGE = 16,  // a wrapped coordinate beyond kMaxCoordBohr
 };
+// Largest |coordinate| (bohr) after wrapping: the 2^-10 bohr grid split of a
+// position is exact in FP32 below 2^13 bohr; the rest is margin for images.
+constexpr float kMaxCoordBohr = 8000.0f;
 
 // Per-structure geometry, computed on the host from the cell and pbc.
 struct StructGeo {

@@ -121,6 +121,20 @@ def test_status_codes(torch_cuda):
     with pytest.raises(D3Error) as e:
         d3c.compute_batch(pos, typ, b.offsets, np.zeros((1, 9)), b.pbc)
     assert e.value.status == _lib.D3_ERR_ARG
+    # coordinates beyond the supported range (|x| < 4200 A after wrapping): a
+    # position along an open axis, reported on the device; a cell, at the call
+    d3d = handle(b.tables)
+    far = pos.clone()
+    far[0, 0] = 5000.0
+    with pytest.raises(D3Error) as e:
+        d3d.compute_batch(far, typ, b.offsets, b.cells, np.zeros_like(b.pbc))
+        d3d.sync_status()
+    assert e.value.status == _lib.D3_ERR_ARG
+    big = np.array(b.cells, dtype=np.float64).reshape(-1, 9).copy()
+    big[:, 0] = 5000.0
+    with pytest.raises(D3Error) as e:
+        d3d.compute_batch(pos, typ, b.offsets, big, b.pbc)
+    assert e.value.status == _lib.D3_ERR_ARG
     # the handle stays usable after reported errors
     out = d3c.compute_batch(pos, typ, b.offsets, b.cells, b.pbc)
     d3c.sync_status()

@@ -251,7 +251,7 @@ def count_triangles(torch, batch, rc, dev):
     return tot
 
 
-def md_leg(torch, dev, params, steps, warmup=3, skin=1.0, dt=0.5, T_K=300.0):
+def md_leg(torch, dev, params, steps, warmup=3, skin=0.5, dt=0.5, T_K=300.0):
     """Velocity-Verlet NVE loop on the 1,048,576-atom box with Verlet-list reuse:
     the library rebuilds the lists (on the device) only when an atom moved more
     than skin/2.  One step = half kick, drift, D3 forces, half kick; the timed
@@ -365,6 +365,8 @@ def main():
     ap.add_argument("--no-graphs", action="store_true", help="enqueue every kernel directly (no graph replay)")
     ap.add_argument("--md-steps", type=int, default=100,
                     help="NVE steps of the 1M-atom box leg with list reuse (0: skip)")
+    ap.add_argument("--md-skin", type=float, default=0.5,
+                    help="Verlet skin (A) of the NVE leg (0.5 A was fastest of 0.5 / 0.75 / 1.0 / 1.5)")
     ap.add_argument("--three-body-steps", type=int, default=5,
                     help="steps of the extra leg with the optional three-body term (0: skip)")
     args = ap.parse_args()
@@ -481,7 +483,7 @@ def main():
                       "flop_per_triangle": None}
 
     # the 1M-atom box as an MD loop, with the lists reused between rebuilds
-    md = md_leg(torch, dev, params, args.md_steps) if args.md_steps > 0 else None
+    md = md_leg(torch, dev, params, args.md_steps, skin=args.md_skin) if args.md_steps > 0 else None
 
     # end to end through the host-memory entry point (pinned buffers, copies inside)
     e2e = None

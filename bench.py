@@ -295,6 +295,35 @@ def md_leg(torch, dev, params, steps, warmup=3, skin=0.5, dt=0.5, T_K=300.0):
             "unit": UNIT, "builds_in_timed_steps": int(builds), "l2": "inputs and lists larger than L2"}
 
 
+def backward_leg(torch, dev, params, steps, warmup=3):
+    """The hand-written backward (dL/d(s6, s8, a1, a2) and dL/dx) of a mixed
+    handle on the damping-refit batch, beside the forward on the same batch."""
+    from paper_2310_05279_gb300 import D3, workloads as wl
+    b = wl.fit_batch()
+    d3 = D3(b.tables, params, precision="mixed")
+    pos = torch.tensor(b.pos, dtype=torch.float64, device=dev)
+    typ = torch.tensor(b.types, dtype=torch.int32, device=dev)
+    g = np.random.Generator(np.random.PCG64(4))
+    dLdE = torch.tensor(g.normal(size=b.nstruct), dtype=torch.float64, device=dev)
+    dLdF = torch.tensor(0.01 * g.normal(size=(b.natoms, 3)), dtype=torch.float64, device=dev)
+    out = d3.compute_batch(pos, typ, b.offsets, b.cells, b.pbc)
+    d3.sync_status()
+
+    def fwd():
+        d3.compute_batch(pos, typ, b.offsets, b.cells, b.pbc, out=out)
+
+    def bwd():
+        d3.backward(pos, typ, b.offsets, b.cells, b.pbc, dLdE, dLdF)
+    tf = time_steps(torch, fwd, steps, warmup)
+    tb = time_steps(torch, bwd, steps, warmup)
+    d3.sync_status()
+    mf, mb = sum(tf) / len(tf), sum(tb) / len(tb)
+    return {"workload": f"fit_batch: {b.nstruct} structures of 200-2000 atoms ({b.natoms:,} atoms), mixed handle",
+            "forward_ms": mf, "backward_ms": mb, "backward_over_forward": mb / mf,
+            "value": b.natoms / (mb * 1e-3), "unit": UNIT,
+            "what": "dL/d(s6, s8, a1, a2) and dL/dx for upstream dL/dE, dL/dF (forward-mode, neighbour build included)"}
+
+
 def cpu_baseline(batch, params, budget_s=15.0):
     """The FP64 oracle, as it stands, on a bounded sample of the workload's structures."""
     import oracle
@@ -367,6 +396,7 @@ def main():
                     help="NVE steps of the 1M-atom box leg with list reuse (0: skip)")
     ap.add_argument("--md-skin", type=float, default=0.5,
                     help="Verlet skin (A) of the NVE leg (0.5 A was fastest of 0.5 / 0.75 / 1.0 / 1.5)")
+    ap.add_argument("--backward-steps", type=int, default=5, help="steps of the backward leg (0: skip)")
     ap.add_argument("--three-body-steps", type=int, default=5,
                     help="steps of the extra leg with the optional three-body term (0: skip)")
     args = ap.parse_args()
@@ -482,6 +512,9 @@ def main():
                       "params": atm, "note": "optional triple-dipole term; the paper's model leaves it out",
                       "flop_per_triangle": None}
 
+    # the hand-written backward on the damping-refit batch
+    backward = backward_leg(torch, dev, params, args.backward_steps) if args.backward_steps > 0 else None
+
     # the 1M-atom box as an MD loop, with the lists reused between rebuilds
     md = md_leg(torch, dev, params, args.md_steps, skin=args.md_skin) if args.md_steps > 0 else None
 
@@ -552,6 +585,7 @@ def main():
             "fp64_form": fp64,
             "three_body": three_body,
             "md_loop": md,
+            "backward": backward,
             "e2e": e2e,
             "gpu_launches": int(round(launches_per_step * args.steps)),
             "gpu_launches_per_step": launches_per_step,

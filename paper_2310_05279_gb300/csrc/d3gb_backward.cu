@@ -191,12 +191,6 @@ __global__ void kb_weights(Work w, BW b, BConsts c, const double* __restrict__ c
 #pragma unroll
             for (int bb = 0; bb < R; ++bb) s += cu[a * R + bb] * L[bb];
             b.v[(p * c.T + u) * R + a] = s;
-            b.vf[(p * c.T + u) * 2 * b.RP + a] = (float)s.v;
-            b.vf[(p * c.T + u) * 2 * b.RP + b.RP + a] = (float)s.t;
-        }
-        for (int a = R; a < b.RP; ++a) {
-            b.vf[(p * c.T + u) * 2 * b.RP + a] = 0.0f;
-            b.vf[(p * c.T + u) * 2 * b.RP + b.RP + a] = 0.0f;
         }
     }
 }

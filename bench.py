@@ -453,6 +453,7 @@ def main():
         torch.distributed.barrier()
     clocks = clk.stop()
     launches_per_step = d3.profile_read()["launches"] / max(1, args.steps)
+    shapes = d3.launch_shapes()
     d3.sync_status()
     ms = reduce_max(sum(times) / len(times), dev)
     value = job_value(N, world, ms * 1e-3)
@@ -573,6 +574,7 @@ def main():
                        "precision": "mixed (FP32 pair math, FP64 accumulation)", "rc_disp_A": 12.0, "rc_cn_A": 6.0,
                        "neighbour_build": "every step", "l2": "flushed between timed steps",
                        "launch": "direct" if args.no_graphs else "graph replay of the steady-state call",
+                       "launch_shapes": {**shapes, "how": "measured by the library's autotuner at plan time"},
                        "parallelism": f"data-parallel x{world}: each rank its own 128-structure scan "
                                       "(jitter seed 1 + rank), no collective on the data path"},
             "roofline": roof,

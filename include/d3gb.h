@@ -126,6 +126,32 @@ d3_status d3_set_graphs(d3_handle *h, int32_t on);
  * always overwritten.  Default off.  Applies to work enqueued afterwards. */
 d3_status d3_set_accumulate(d3_handle *h, int32_t on);
 
+/* Launch shapes of the hot kernels, as int32_t shapes[4]: threads per block
+ * of the CN pass (Eq. 4 with the Eq. 3 weights), of the dispersion pass
+ * (Eq. 2) and of the CN chain-rule pass (64 or 128 each), and blocks per SM of
+ * the persistent neighbour-list builder (8 or 16).  Every choice gives
+ * bit-identical results; only the time differs.
+ *
+ * Autotuning (default on): when a new geometry of at least 16384 atoms is
+ * sized, the library runs the build and the passes three times with each
+ * candidate, timed with CUDA events on the call's stream, and keeps per kernel
+ * the faster shape (the default unless the other is more than 1% faster).  The
+ * choice is cached per size class (precision, three-body term on or off, and
+ * the binary orders of magnitude of the atom count and of the mean structure
+ * size), so later geometries of the same class reuse it.  Smaller geometries
+ * use the defaults {64, 128, 128, 16}.  The measurement runs write only the
+ * library's workspace, leave the build count unchanged and count as launches.
+ *
+ * d3_set_autotune: on = 0 keeps the current shapes for later geometries.
+ * d3_launch_shapes: the shapes used for work enqueued next (host int32_t[4],
+ * may be NULL) and the number of measurements made so far (host, may be NULL).
+ * d3_set_launch_shapes: fix the shapes (host int32_t[4]) and turn autotuning
+ * off; D3_ERR_ARG if a value is not one of the candidates, and then nothing
+ * changes.  Applies to work enqueued afterwards. */
+d3_status d3_set_autotune(d3_handle *h, int32_t on);
+d3_status d3_launch_shapes(d3_handle *h, int32_t *shapes, int64_t *tunings);
+d3_status d3_set_launch_shapes(d3_handle *h, const int32_t *shapes);
+
 /* Optional three-body term (off by default).  The paper's model is two-body:
  * Sec. II A leaves out the triple-dipole term of the original D3 model, and so
  * does every other entry point unless this one enables it.  With s9 != 0 the

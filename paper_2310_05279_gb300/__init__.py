@@ -222,6 +222,25 @@ class D3:
         """Replay repeated compute calls as one CUDA graph (default on)."""
         self._check(self.lib.d3_set_graphs(self.h, 1 if on else 0))
 
+    SHAPE_KEYS = ("cn_block", "disp_block", "chain_block", "build_blocks_per_sm")
+
+    def set_autotune(self, on: bool = True):
+        """Measure the launch shapes once per size class when a new geometry is sized (default on)."""
+        self._check(self.lib.d3_set_autotune(self.h, 1 if on else 0))
+
+    def launch_shapes(self) -> dict:
+        """Launch shapes used for the next call, and the number of autotuner measurements so far."""
+        sh = (C.c_int32 * 4)()
+        n = C.c_int64()
+        self._check(self.lib.d3_launch_shapes(self.h, sh, C.byref(n)))
+        return dict(zip(self.SHAPE_KEYS, list(sh)), tunings=n.value)
+
+    def set_launch_shapes(self, cn_block: int, disp_block: int, chain_block: int, build_blocks_per_sm: int):
+        """Fix the launch shapes (64 or 128 threads per pass block, 8 or 16 builder blocks per SM);
+        turns autotuning off."""
+        sh = (C.c_int32 * 4)(cn_block, disp_block, chain_block, build_blocks_per_sm)
+        self._check(self.lib.d3_set_launch_shapes(self.h, sh))
+
     def set_three_body(self, s9: float = 1.0, alpha9: float = 16.0, rc3: Optional[float] = None):
         """Optional triple-dipole term that the paper leaves out (d3_set_three_body): s9 = 0 turns it
         off; rc3 (A, default R_cn) bounds every side of a triangle and may not exceed R_cn."""

@@ -49,6 +49,9 @@ SIGNATURES = {
     "d3_set_accumulate": (C.c_int, [_vp, C.c_int32]),
     "d3_set_three_body": (C.c_int, [_vp, C.c_double, C.c_double, C.c_double]),
     "d3_set_graphs": (C.c_int, [_vp, C.c_int32]),
+    "d3_set_autotune": (C.c_int, [_vp, C.c_int32]),
+    "d3_launch_shapes": (C.c_int, [_vp, _ip, _lp]),
+    "d3_set_launch_shapes": (C.c_int, [_vp, _ip]),
     "d3_version": (C.c_char_p, []),
     "d3_profile_enable": (C.c_int, [_vp, C.c_int32]),
     "d3_profile_read": (C.c_int, [_vp, _dp, _lp, _lp]),

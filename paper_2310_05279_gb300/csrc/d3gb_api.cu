@@ -9,10 +9,12 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -37,6 +39,18 @@ namespace {
 constexpr int kWindowCells = 3;  // list radius spans at most this many cells per axis
 // profiled stages: build, CN (with the Eq. 3 weights), weights, dispersion, three-body, chain, finalize
 constexpr int kStages = 7;
+
+// Launch shapes: threads per block of the CN, dispersion and chain passes, and
+// list-builder blocks per SM.  The defaults are the fastest shapes on the
+// 128 x 1440 bilayer scan; the autotuner measures the candidates once per size
+// class.  Every candidate gives bit-identical results: the passes run one
+// thread per atom with per-thread sums, and each list row is written by one
+// lane in a fixed walk order whichever warp takes it.
+constexpr int32_t kDefaultShape[4] = {64, 128, 128, 16};
+constexpr int32_t kBlockCand[2] = {64, 128};
+constexpr int32_t kBuildCand[2] = {8, 16};
+constexpr int64_t kTuneMinAtoms = 16384;  // below this launch overhead decides, not the shape
+constexpr int kTuneReps = 3;
 
 struct DevBuf {
     std::vector<void*> ptrs;
@@ -120,6 +134,11 @@ struct d3_handle {
     int64_t glaunches = 0;         // kernels in the captured call
     const void* gkey[10] = {};     // pointers and generations the graph was captured with
     int64_t plan_gen = 0, param_gen = 0;
+    // launch shapes (d3_launch_shapes): chosen per size class by the autotuner unless fixed
+    int32_t shape[4] = {kDefaultShape[0], kDefaultShape[1], kDefaultShape[2], kDefaultShape[3]};
+    bool autotune = true;
+    int64_t tunings = 0;
+    std::map<std::array<int, 4>, std::array<int32_t, 4>> shape_cache;
 };
 
 namespace {
@@ -347,6 +366,10 @@ d3_status plan_alloc(d3_handle* h, Plan& P) {
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         w.num_sms = sms > 0 ? sms : 1;
     }
+    w.blk_cn = h->shape[0];
+    w.blk_disp = h->shape[1];
+    w.blk_chain = h->shape[2];
+    w.build_per_sm = h->shape[3];
     const size_t rs = h->prm.precision == D3_MIXED ? sizeof(float) : sizeof(double);
     StructGeo* dgeo = nullptr;
     int64_t* doff = nullptr;
@@ -464,6 +487,51 @@ std::vector<cudaEvent_t> take_events(d3_handle* h, int n) {
     return v;
 }
 
+// Device tables of the forward passes for the handle's precision.
+Tabs forward_tabs(const d3_handle* h) {
+    const bool mixed = h->prm.precision == D3_MIXED;
+    Tabs tb{};
+    tb.c6 = mixed ? (const void*)h->d_c6f : (const void*)h->d_c6d;
+    tb.pair = mixed ? (const void*)h->d_pairf : (const void*)h->d_paird;
+    tb.cnref = h->d_cnref;
+    tb.cnref2 = h->d_cnref2;
+    tb.dcr = h->d_dcr;
+    tb.nref = h->d_nref;
+    tb.rcpair = h->d_rcpair;
+    tb.exptab = h->d_exptab;
+    tb.rtab = mixed ? (const void*)h->d_rtabf : (const void*)h->d_rtabd;
+    return tb;
+}
+
+void set_shapes(d3_handle* h, const int32_t* shape) {
+    bool changed = false;
+    for (int k = 0; k < 4; ++k) {
+        changed = changed || h->shape[k] != shape[k];
+        h->shape[k] = shape[k];
+    }
+    Work& w = h->plan.w;
+    w.blk_cn = shape[0];
+    w.blk_disp = shape[1];
+    w.blk_chain = shape[2];
+    w.build_per_sm = shape[3];
+    if (changed) ++h->param_gen;  // launch shapes are baked into a captured graph
+}
+
+// Size class of a plan for the autotuner: precision, three-body term on or
+// off, and the binary orders of magnitude of the atom count and of the mean
+// structure size.
+std::array<int, 4> size_class(const d3_handle* h, const Plan& P) {
+    auto lg = [](int64_t x) {
+        int k = 0;
+        while (x > 1) {
+            x >>= 1;
+            ++k;
+        }
+        return k;
+    };
+    return {h->prm.precision, h->s9 != 0.0 ? 1 : 0, lg(P.Nr), lg(P.Nr / std::max(P.B, 1))};
+}
+
 // Enqueue the neighbour build.  gated (list reuse, skin > 0): a displacement
 // check first decides on the device whether the build runs; the sorted
 // positions are rewritten either way.
@@ -481,6 +549,86 @@ d3_status enqueue_build(d3_handle* h, Plan& P, const double* pos, const int32_t*
     e = launch_build_impl(w, pos, types, h->d_rk, P.bsum, st);
     if (e != cudaSuccess) return cuda_fail(h, e, "neighbour build launch");
     if (P.Nr > 0) h->launches += kBuildLaunches;
+    return D3_OK;
+}
+
+// The autotuner: once per size class, right after a new geometry is sized,
+// run the build and the forward passes kTuneReps times with each candidate
+// shape (alternating) and keep, per kernel, the candidate with the shortest
+// time; a candidate replaces the default only when it is more than 1% faster.
+// Each stage is timed with events on the caller's stream.  The runs write
+// only the plan's workspace and scratch outputs, and the device build counter
+// is put back afterwards.
+d3_status tune_shapes(d3_handle* h, Plan& P, const double* pos, const int32_t* types, cudaStream_t st) {
+    if (!h->autotune) return D3_OK;
+    if (P.Nr < kTuneMinAtoms) {
+        set_shapes(h, kDefaultShape);
+        return D3_OK;
+    }
+    const std::array<int, 4> key = size_class(h, P);
+    const auto it = h->shape_cache.find(key);
+    if (it != h->shape_cache.end()) {
+        set_shapes(h, it->second.data());
+        return D3_OK;
+    }
+    std::vector<cudaEvent_t> ev = take_events(h, kStages + 1);
+    auto give_back = [&]() {
+        for (cudaEvent_t x : ev) h->ev_pool.push_back(x);
+    };
+    if (ev.size() != kStages + 1) {
+        give_back();
+        return cuda_fail(h, cudaErrorMemoryAllocation, "autotuner events");
+    }
+    DevBuf scratch;
+    double *E = nullptr, *F = nullptr, *W = nullptr;
+    cudaError_t e = scratch.alloc(&E, (size_t)P.B);
+    if (e == cudaSuccess) e = scratch.alloc(&F, 3 * (size_t)P.Nr);
+    if (e == cudaSuccess) e = scratch.alloc(&W, 9 * (size_t)P.B);
+    unsigned long long nbuild = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&nbuild, h->d_nbuild, sizeof(nbuild), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    Consts c = make_consts(h);
+    c.accumulate = 0;
+    const Tabs tb = forward_tabs(h);
+    const bool mixed = h->prm.precision == D3_MIXED;
+    Work w = P.w;
+    // t[kernel][candidate]: build, CN, dispersion, chain
+    float t[4][2];
+    for (auto& r : t) r[0] = r[1] = 1e30f;
+    for (int rep = 0; rep < kTuneReps && e == cudaSuccess; ++rep) {
+        for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+            w.build_per_sm = kBuildCand[k];
+            w.blk_cn = w.blk_disp = w.blk_chain = kBlockCand[k];
+            e = cudaEventRecord(ev[0], st);
+            if (e == cudaSuccess) e = launch_build_impl(w, pos, types, h->d_rk, P.bsum, st);
+            // marks 0..6 of the forward land in ev[1..7]: CN 0-1, dispersion 2-3, chain 4-5
+            if (e == cudaSuccess) e = launch_forward(w, c, mixed, tb, E, F, W, nullptr, nullptr, nullptr, P.B, st,
+                                                     ev.data() + 1);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            h->launches += kBuildLaunches + kForwardLaunches + c.atm;
+            const int from[4] = {0, 1, 3, 5};
+            for (int m = 0; m < 4 && e == cudaSuccess; ++m) {
+                float ms = 0.f;
+                e = cudaEventElapsedTime(&ms, ev[from[m]], ev[from[m] + 1]);
+                t[m][k] = std::min(t[m][k], ms);
+            }
+        }
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_nbuild, &nbuild, sizeof(nbuild), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    scratch.release();
+    give_back();
+    if (e != cudaSuccess) return cuda_fail(h, e, "autotuner");
+    // kernel m's default is candidate dflt[m]; the other must beat it by more than 1%
+    const int dflt[4] = {kDefaultShape[3] == kBuildCand[0] ? 0 : 1, kDefaultShape[0] == kBlockCand[0] ? 0 : 1,
+                         kDefaultShape[1] == kBlockCand[0] ? 0 : 1, kDefaultShape[2] == kBlockCand[0] ? 0 : 1};
+    int pick[4];
+    for (int m = 0; m < 4; ++m) pick[m] = t[m][1 - dflt[m]] < 0.99f * t[m][dflt[m]] ? 1 - dflt[m] : dflt[m];
+    const std::array<int32_t, 4> chosen = {kBlockCand[pick[1]], kBlockCand[pick[2]], kBlockCand[pick[3]],
+                                           kBuildCand[pick[0]]};
+    h->shape_cache[key] = chosen;
+    ++h->tunings;
+    set_shapes(h, chosen.data());
     return D3_OK;
 }
 
@@ -535,7 +683,7 @@ d3_status ensure_plan(d3_handle* h, int32_t B, const int64_t* offsets, const dou
         }
         if (!grow) {
             P.sized = true;
-            return D3_OK;
+            return tune_shapes(h, P, pos, types, st);
         }
         s = plan_alloc(h, P);
         if (s != D3_OK) return s;
@@ -579,16 +727,7 @@ d3_status forward(d3_handle* h, int32_t B, const int64_t* offsets, const double*
     if (s != D3_OK) return s;
     const Consts c = make_consts(h);
     const bool mixed = h->prm.precision == D3_MIXED;
-    Tabs tb;
-    tb.c6 = mixed ? (const void*)h->d_c6f : (const void*)h->d_c6d;
-    tb.pair = mixed ? (const void*)h->d_pairf : (const void*)h->d_paird;
-    tb.cnref = h->d_cnref;
-    tb.cnref2 = h->d_cnref2;
-    tb.dcr = h->d_dcr;
-    tb.nref = h->d_nref;
-    tb.rcpair = h->d_rcpair;
-    tb.exptab = h->d_exptab;
-    tb.rtab = mixed ? (const void*)h->d_rtabf : (const void*)h->d_rtabd;
+    const Tabs tb = forward_tabs(h);
     cudaError_t e = launch_forward(P.w, c, mixed, tb, E, F, W, e_atom, cn, w_atom, B, st,
                                    ev.size() == kStages + 1 ? ev.data() + 1 : nullptr);
     if (e != cudaSuccess) return cuda_fail(h, e, "forward launch");
@@ -836,6 +975,33 @@ d3_status d3_set_graphs(d3_handle* h, int32_t on) {
 d3_status d3_set_accumulate(d3_handle* h, int32_t on) {
     if (!h) return D3_ERR_ARG;
     h->accumulate = on != 0;
+    return D3_OK;
+}
+
+d3_status d3_set_autotune(d3_handle* h, int32_t on) {
+    if (!h) return D3_ERR_ARG;
+    h->autotune = on != 0;
+    return D3_OK;
+}
+
+d3_status d3_launch_shapes(d3_handle* h, int32_t* shapes, int64_t* tunings) {
+    if (!h) return D3_ERR_ARG;
+    if (shapes)
+        for (int k = 0; k < 4; ++k) shapes[k] = h->shape[k];
+    if (tunings) *tunings = h->tunings;
+    return D3_OK;
+}
+
+d3_status d3_set_launch_shapes(d3_handle* h, const int32_t* shapes) {
+    if (!h) return D3_ERR_ARG;
+    if (!shapes) return fail(h, D3_ERR_ARG, "NULL shapes");
+    for (int k = 0; k < 3; ++k)
+        if (shapes[k] != kBlockCand[0] && shapes[k] != kBlockCand[1])
+            return fail(h, D3_ERR_ARG, "pass blocks must have 64 or 128 threads");
+    if (shapes[3] != kBuildCand[0] && shapes[3] != kBuildCand[1])
+        return fail(h, D3_ERR_ARG, "the list builder takes 8 or 16 blocks per SM");
+    h->autotune = false;
+    set_shapes(h, shapes);
     return D3_OK;
 }
 

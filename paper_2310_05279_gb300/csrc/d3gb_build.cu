@@ -682,10 +682,9 @@ cudaError_t launch_build_impl(const Work& w, const double* pos, const int32_t* t
     k_fill_real<<<nblk(w.Nr, TB), TB, 0, st>>>(w, types, rk_tab);
     if (w.ghost_cap > 0) k_fill_ghost<<<nblk(w.ghost_cap, TB), TB, 0, st>>>(w, types, rk_tab);
     {
-        // persistent warps: enough blocks to fill every SM, work handed out per 32 atoms
-        // (16 blocks of 128 per SM build the scan's lists 3.5 us faster than 8)
+        // persistent warps: w.build_per_sm blocks per SM, work handed out per 32 atoms
         const int chunks = (int)((w.Nr + 31) / 32);
-        const int blocks = std::min((chunks + 3) / 4, w.num_sms * 16);
+        const int blocks = std::min((chunks + 3) / 4, w.num_sms * w.build_per_sm);
         k_build_lists<<<blocks, 128, 0, st>>>(w);
     }
     return cudaGetLastError();

@@ -120,6 +120,9 @@ struct Work {
     double skin_half2;       // (skin / 2)^2, bohr^2
     unsigned long long* nbuild;  // [1] builds executed
     int num_sms;
+    // launch shapes (read on the host when enqueueing; every choice gives the same results)
+    int blk_cn, blk_disp, blk_chain;  // threads per block of the CN, dispersion and chain passes
+    int build_per_sm;                 // list-builder blocks per SM
     float rl_disp2, rl_cn2;  // list radii squared, bohr^2
     // passes
     double* cn;              // [Nr]

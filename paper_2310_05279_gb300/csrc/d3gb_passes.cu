@@ -536,28 +536,23 @@ __global__ void __launch_bounds__(128) k_fin_struct(Work w, const double* __rest
 
 inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
-// Launch shapes, measured on the 128 x 1440 scan (same-box A/B): 64-thread
-// blocks make the CN pass 2 us faster and the dispersion pass 10 us slower than
-// 128; the chain pass does not care.
-constexpr int kCnBlock = 64;
-
 template <bool MIXED, int R>
 cudaError_t forward_impl(const Work& w, const Consts& c, const Tabs& tb, double* E, double* F, double* W,
                          double* e_atom, double* cn_out, double* w_atom, int B, cudaStream_t st,
                          cudaEvent_t* marks) {
     using T = typename Real<MIXED>::T;
     using T4 = typename Real<MIXED>::T4;
-    const int TB = 128;
     auto mark = [&](int k) {
         if (marks) cudaEventRecord(marks[k], st);
     };
     mark(0);
     if (w.Nr > 0)
-        k_cn<MIXED, R><<<nblk(w.Nr, kCnBlock), kCnBlock, 0, st>>>(w, c, tb.rcpair, tb.exptab, tb.cnref, tb.cnref2,
+        k_cn<MIXED, R><<<nblk(w.Nr, w.blk_cn), w.blk_cn, 0, st>>>(w, c, tb.rcpair, tb.exptab, tb.cnref, tb.cnref2,
                                                                   tb.dcr, tb.nref, (const T*)tb.c6);
     mark(1);  // the weights (Eq. 3) are formed inside the CN pass
     mark(2);
     if (w.Nr > 0) {
+        const int TB = w.blk_disp;
         if (w_atom)
             k_disp<MIXED, R, true><<<nblk(w.Nr, TB), TB, c.T * c.T * sizeof(T4), st>>>(w, c, (const T4*)tb.pair);
         else
@@ -570,6 +565,7 @@ cudaError_t forward_impl(const Work& w, const Consts& c, const Tabs& tb, double*
     }
     mark(4);
     if (w.Nr > 0) {
+        const int TB = w.blk_chain;
         if (w_atom)
             k_chain<MIXED, true><<<nblk(w.Nr, TB), TB, 0, st>>>(w, c, tb.rcpair, tb.exptab, F, e_atom, cn_out, w_atom);
         else

@@ -6,4 +6,5 @@ imports this package.  The arithmetic lives in ``d3_oracle.c``; this module
 compiles it with gcc (``build()``) and calls it through ctypes.
 """
 from .oracle import (build, compute, compute_batch, weights, params_from, lib_path,  # noqa: F401
-                     num_threads, atom_virial, atom_virial_batch)
+                     num_threads, atom_virial, atom_virial_batch, compile_library, using_library,
+                     source_path)

@@ -10,6 +10,7 @@ parameters adds the optional three-body term (see ``atm_triangle`` in the C sour
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes as C
 import os
 import subprocess
@@ -27,13 +28,23 @@ def lib_path() -> str:
     return _LIB
 
 
+def source_path() -> str:
+    return _SRC
+
+
+def compile_library(src: str, out: str) -> str:
+    """Compile an oracle source file with gcc (-O2, OpenMP, no fast-math, no FMA contraction)."""
+    tmp = out + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-ffp-contract=off",
+                           "-o", tmp, src, "-lm"])
+    os.replace(tmp, out)
+    return out
+
+
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (-O2, OpenMP, no fast-math, no FMA contraction)."""
+    """Compile d3_oracle.c into liboracle_d3.so next to it (when missing or older than the source)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-ffp-contract=off",
-                               "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB)
+        compile_library(_SRC, _LIB)
     return _LIB
 
 
@@ -48,23 +59,41 @@ class _Tables(C.Structure):
                 ("rcov", C.POINTER(C.c_double)), ("sqrtq", C.POINTER(C.c_double))]
 
 
+def _bind(path: str):
+    lib = C.CDLL(path)
+    d = C.POINTER(C.c_double)
+    lib.d3_oracle_compute.restype = C.c_int
+    lib.d3_oracle_compute.argtypes = [C.POINTER(_Params), C.POINTER(_Tables), C.c_int64, d,
+                                      C.POINTER(C.c_int32), d, C.POINTER(C.c_int32), d, d, d, d, d, d, d]
+    lib.d3_oracle_weights.restype = None
+    lib.d3_oracle_weights.argtypes = [C.POINTER(_Tables), C.c_int, C.c_double, C.c_double, d, d]
+    lib.d3_oracle_num_threads.restype = C.c_int
+    lib.d3_oracle_atom_virial.restype = C.c_int
+    lib.d3_oracle_atom_virial.argtypes = [C.POINTER(_Params), C.POINTER(_Tables), C.c_int64, d,
+                                          C.POINTER(C.c_int32), d, C.POINTER(C.c_int32), d]
+    return lib
+
+
 def _load():
     global _lib
     if _lib is None:
         build()
-        lib = C.CDLL(_LIB)
-        d = C.POINTER(C.c_double)
-        lib.d3_oracle_compute.restype = C.c_int
-        lib.d3_oracle_compute.argtypes = [C.POINTER(_Params), C.POINTER(_Tables), C.c_int64, d,
-                                          C.POINTER(C.c_int32), d, C.POINTER(C.c_int32), d, d, d, d, d, d, d]
-        lib.d3_oracle_weights.restype = None
-        lib.d3_oracle_weights.argtypes = [C.POINTER(_Tables), C.c_int, C.c_double, C.c_double, d, d]
-        lib.d3_oracle_num_threads.restype = C.c_int
-        lib.d3_oracle_atom_virial.restype = C.c_int
-        lib.d3_oracle_atom_virial.argtypes = [C.POINTER(_Params), C.POINTER(_Tables), C.c_int64, d,
-                                              C.POINTER(C.c_int32), d, C.POINTER(C.c_int32), d]
-        _lib = lib
+        _lib = _bind(_LIB)
     return _lib
+
+
+@contextlib.contextmanager
+def using_library(path: str):
+    """Route every call of this module through another build of the oracle's C
+    source (the tests compile copies with one planted mistake to check that the
+    pins catch it); the default library is restored on exit."""
+    global _lib
+    saved = _load()
+    _lib = _bind(path)
+    try:
+        yield
+    finally:
+        _lib = saved
 
 
 def num_threads() -> int:

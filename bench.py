@@ -110,9 +110,9 @@ def kernel_source_sha(path: str, kernel: str):
     return None
 
 
-def recorded_traffic(kernel: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None
-    when the kernel's definition has changed since the counters were taken."""
+def recorded_counters(kernel: str):
+    """The committed ncu record of `kernel` (profiles/traffic.json), or None when
+    the kernel's definition has changed since the counters were taken."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
@@ -123,7 +123,20 @@ def recorded_traffic(kernel: str):
     src = os.path.join(ROOT, rec["source"])
     if not os.path.exists(src) or kernel_source_sha(src, kernel) != rec.get("kernel_sha256"):
         return None
-    return float(rec["dram_bytes_per_launch"])
+    return rec
+
+
+def recorded_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu capture, or None."""
+    rec = recorded_counters(kernel)
+    return float(rec["dram_bytes_per_launch"]) if rec else None
+
+
+def recorded_pipes(kernel: str):
+    """Pipe utilisation of `kernel` from the committed ncu capture (percent of
+    peak), or None: which unit the kernel is actually bound by."""
+    rec = recorded_counters(kernel)
+    return rec.get("pipes") if rec else None
 
 
 def measured_peaks():
@@ -553,7 +566,7 @@ def main():
     disp_tflops = disp_flops_per_pair(nref) * pairs / (stage_ms["disp"] * 1e-3) / 1e12
     roof = {"bound": "alu", "kernel": "k_disp (dispersion pass, Eq. 2)", "achieved": disp_tflops,
             "peak": fp32_peak, "unit": "TFLOP/s", "frac": disp_tflops / fp32_peak,
-            "traffic": recorded_traffic("k_disp"),
+            "traffic": recorded_traffic("k_disp"), "pipes": recorded_pipes("k_disp"),
             "peak_source": f"{sm_count} SMs x 128 FP32 lanes x 2 x {fmax/1e6:.0f} MHz (sm_max_mhz, {peak_kind})",
             "algorithmic": f"{disp_flops_per_pair(nref)} FLOP per unique pair within 12 A x {pairs:.4g} pairs",
             "timing": "k_disp stage events over the same number of steps, kernels enqueued directly"}
@@ -564,6 +577,7 @@ def main():
         three_body["flop_per_triangle"] = fl
         three_body["roofline"] = {"bound": "alu", "kernel": "k_atm", "achieved": tf, "peak": fp32_peak,
                                   "unit": "TFLOP/s", "frac": tf / fp32_peak, "traffic": recorded_traffic("k_atm"),
+                                  "pipes": recorded_pipes("k_atm"),
                                   "algorithmic": f"{fl} FLOP per unique triangle x {three_body['triangles']:.4g}"}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -80,14 +80,16 @@ def test_recorded_traffic_tracks_source(tmp_path, monkeypatch):
     helpers.write_text("// helpers v1\n")
     (tmp_path / "profiles").mkdir()
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    rec = {"k": {"dram_bytes_per_launch": 123.0, "source": "k.cu",
+    rec = {"k": {"dram_bytes_per_launch": 123.0, "source": "k.cu", "pipes": {"fma_pipe": 50.0},
                  "kernel_sha256": bench.kernel_source_sha(str(src), "k")}}
     (tmp_path / "profiles" / "traffic.json").write_text(json.dumps(rec))
     assert bench.recorded_traffic("k") == 123.0
+    assert bench.recorded_pipes("k") == {"fma_pipe": 50.0}
     src.write_text(other.replace("x += 1", "x += 3") + kern)  # another kernel changed: still valid
     assert bench.recorded_traffic("k") == 123.0
     src.write_text(other + kern.replace("x += 2", "x += 4"))  # the kernel changed
     assert bench.recorded_traffic("k") is None
+    assert bench.recorded_pipes("k") is None
     src.write_text(other + kern)
     assert bench.recorded_traffic("k") == 123.0
     helpers.write_text("// helpers v2\n")  # an inlined helper changed

@@ -7,7 +7,8 @@
  * the C6 interpolation of Eq. 3 over the coordination numbers of Eq. 4, the
  * forces of Eqs. 5-6 (evaluated as F = -dE/dx including the dependence on
  * neighbours' coordination numbers) and the total of the per-atom virials of
- * Eq. 7.  The three-body term is excluded, as in the paper.
+ * Eq. 7.  The three-body term is excluded by default, as in the paper;
+ * d3_set_three_body adds it as an option.
  *
  * Conventions shared by every entry point
  *  - Units: positions and cells in Angstrom; a2, covalent radii and sqrt(Q) in
@@ -24,7 +25,9 @@
  *  - Work is enqueued on the caller's stream (a cudaStream_t passed as void*;
  *    NULL = legacy default stream).  Unless stated otherwise a call does not
  *    synchronise.  The first call for a new batch geometry (offsets, cells,
- *    pbc) sizes the workspace and synchronises once; later calls with the same
+ *    pbc) sizes the workspace and synchronises once (and, for the first
+ *    geometry of a size class, measures the launch shapes: d3_set_autotune);
+ *    later calls with the same
  *    geometry allocate nothing and do not synchronise, so they can be captured
  *    in a CUDA graph.
  *  - Errors: every call returns a d3_status.  Device-side problems (capacity

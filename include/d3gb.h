@@ -56,7 +56,7 @@ typedef enum d3_status {
     D3_ERR_CUDA = 2,      /* a CUDA runtime call failed (message in d3_last_error) */
     D3_ERR_CAPACITY = 3,  /* a neighbour or image buffer overflowed; it has been regrown, repeat the call */
     D3_ERR_NONFINITE = 4, /* a coordinate was NaN or infinite */
-    D3_ERR_TIMEOUT = 5,   /* a bounded device wait gave up */
+    D3_ERR_TIMEOUT = 5,   /* reserved: no entry point returns it (the library has no device-side waits) */
     D3_ERR_TYPE = 6,      /* an atom type outside [0, ntypes) */
     D3_ERR_STATE = 7      /* call out of sequence */
 } d3_status;
@@ -284,9 +284,10 @@ d3_status d3_profile_read(d3_handle *h, double *ms, int64_t *calls, int64_t *lau
 d3_status d3_profile_reset(d3_handle *h);
 
 /* Per-structure energies from site energies, for callers that cannot allocate
- * device memory (for example code running while a stream is being captured
- * into a CUDA graph, or a host program that keeps all device memory in its own
- * pool).  The paper has no counterpart: this is a service entry point.
+ * device memory: a host program that keeps all device memory in its own pool
+ * and hands libraries only the buffers it owns, or a loop that cannot take the
+ * implicit device synchronisation a cudaMalloc may cause.  The paper has no
+ * counterpart: this is a service entry point.
  *  B        number of structures, 0 <= B <= 16384
  *  offsets  host int64[B+1], offsets[0] = 0, non-decreasing
  *  e_atom   device double[offsets[B]] site energies (e.g. from d3_compute_batch_ex), eV
@@ -294,11 +295,15 @@ d3_status d3_profile_reset(d3_handle *h);
  * Allocates nothing: its scratch is a fixed array of about 0.7 MB inside the
  * library that every device which loads the library holds until the process
  * exits.  Limit: B times ceil(largest structure / 4096) must not exceed 65536;
- * beyond that (or B > 16384) it returns D3_ERR_CAPACITY.  The first call on a
- * device looks up the array's device address; make that first call before any
- * stream capture.  All calls share the array, so calls that overlap on the GPU
- * race; calls ordered on one stream are safe.  Enqueued on `stream`, no
- * synchronisation, no handle needed. */
+ * beyond that (or B > 16384) it returns D3_ERR_CAPACITY before enqueueing
+ * anything.  The first call on a device looks up the array's device address
+ * (once per device, with that device current); make that first call before
+ * any stream capture.  The address is kept for the life of the process, so
+ * calls after cudaDeviceReset are not supported.  All calls share the array,
+ * so calls that overlap on the GPU race; calls ordered on one stream are
+ * safe.  Enqueued on `stream` (offsets is copied to the device by an
+ * asynchronous copy on that stream: keep it valid and unchanged until the
+ * stream has reached this call), no handle needed. */
 d3_status d3_structure_energies_noalloc(int32_t B, const int64_t *offsets, const double *e_atom, double *E,
                                         void *stream);
 

@@ -68,14 +68,21 @@ struct DevBuf {
     }
 };
 
+// List layout of a build: the mixed form's forward takes its dispersion pairs
+// from cluster half lists (per-atom lists only within R_cn); the FP64 form, the
+// per-atom virial of Eq. 7 and the backward use full per-atom lists.
+enum ListMode { kFullLists = 0, kClusterLists = 1 };
+
 struct Plan {
-    bool valid = false, sized = false;
+    bool valid = false;
+    bool sized[2] = {false, false};  // capacities measured for each list mode
+    int last_mode = -1;              // list mode of the last build enqueued
     int B = 0;
     std::vector<int64_t> offsets;
     std::vector<double> cells;
     std::vector<int32_t> pbc;
     std::vector<StructGeo> geo;
-    int64_t Nr = 0, ncells = 0, list_disp = 0, list_cn = 0;
+    int64_t Nr = 0, ncells = 0, list_disp = 0, list_cn = 0, list_cl = 0, ncl = 0;
     int ghost_cap = 0;
     DevBuf mem;
     Work w{};
@@ -83,7 +90,16 @@ struct Plan {
     int* gate = nullptr;  // list-reuse gate (device int)
     double* bwd_scratch = nullptr;
     int64_t bwd_scratch_n = 0;
+    unsigned long long* acc = nullptr;  // fixed-point sums of the cluster-list dispersion pass
+    float* vd = nullptr;                // C6 projections (v, dv) per atom of the cluster-list dispersion pass
 };
+
+// The plan's Work set up for a list mode (kernel arguments are taken by value).
+void set_mode(Plan& P, int mode) {
+    P.w.cl_mode = mode == kClusterLists ? 1 : 0;
+    P.w.acc = mode == kClusterLists ? P.acc : nullptr;
+    P.w.vd = mode == kClusterLists ? P.vd : nullptr;
+}
 
 }  // namespace
 
@@ -201,6 +217,7 @@ Consts make_consts(const d3_handle* h) {
     Consts c{};
     const double rd = h->prm.rc_disp_A / kBohrA, rn = h->prm.rc_cn_A / kBohrA;
     c.rc_disp2 = rd * rd;
+    c.rc_disp2f = (float)c.rc_disp2;
     c.rc_cn2 = rn * rn;
     c.k1 = h->prm.k1;
     c.k3 = h->prm.k3;
@@ -328,6 +345,9 @@ d3_status plan_geometry(d3_handle* h, Plan& P, int32_t B, const int64_t* offsets
         const double cap_all = (double)n * vol_factor + 8;
         G.cap_disp = round_cap(std::min(cap_all, std::ceil(1.3 * nd + 32.0)));
         G.cap_cn = round_cap(std::min(cap_all, std::ceil(1.3 * nn + 16.0)));
+        // a cluster list holds about half the atoms within the list radius of the
+        // cluster's bounding box (regrown by the sizing pass when short)
+        G.cap_cl = round_cap(std::min(cap_all, std::ceil(4.5 * nd + 64.0)));
         ghost_est[s] = (double)n * (vol_factor - 1.0);
     }
     P.ncells = cell_base;
@@ -342,15 +362,25 @@ d3_status plan_alloc(d3_handle* h, Plan& P) {
     P.bwd_scratch_n = 0;
     const int B = P.B;
     const int64_t Nr = P.Nr, C = P.ncells, Ng = P.ghost_cap, Nt = Nr + Ng;
-    int64_t ld = 0, lc = 0;
+    int64_t ld = 0, lc = 0, lcl = 0, ncl = 0;
+    std::vector<int> clu_sid;
     for (int s = 0; s < B; ++s) {
-        P.geo[s].list_base_disp = ld;
-        P.geo[s].list_base_cn = lc;
-        ld += list_size(P.geo[s].natoms, P.geo[s].cap_disp);
-        lc += list_size(P.geo[s].natoms, P.geo[s].cap_cn);
+        StructGeo& G = P.geo[s];
+        G.list_base_disp = ld;
+        G.list_base_cn = lc;
+        ld += list_size(G.natoms, G.cap_disp);
+        lc += list_size(G.natoms, G.cap_cn);
+        const int64_t k = (G.natoms + kClusterAtoms - 1) / kClusterAtoms;
+        G.clu_base = ncl;
+        G.list_base_cl = lcl;
+        ncl += k;
+        lcl += k * (int64_t)G.cap_cl;
+        clu_sid.insert(clu_sid.end(), (size_t)k, s);
     }
     P.list_disp = ld;
     P.list_cn = lc;
+    P.list_cl = lcl;
+    P.ncl = ncl;
     Work& w = P.w;
     w = Work{};
     w.B = B;
@@ -408,8 +438,15 @@ d3_status plan_alloc(d3_handle* h, Plan& P) {
     A(w.nbr_cn, int, lc);
     A(w.cnt_disp, int, Nr);
     A(w.cnt_cn, int, Nr);
-    A(w.maxcnt, int, 2 * B);
-    A(w.work_ctr, int, 1);
+    A(w.maxcnt, int, 3 * B);
+    A(w.work_ctr, int, 2);
+    A(w.skey, float, Nr);
+    int* dclu = nullptr;
+    A(dclu, int, std::max<int64_t>(1, ncl));
+    A(w.nbr_cl, int, lcl);
+    A(w.cnt_cl, int, std::max<int64_t>(1, ncl));
+    A(w.acc, unsigned long long, 8 * Nr);
+    if (h->prm.precision == D3_MIXED) A(w.vd, float, Nt * h->T * 2 * h->RP);
     A(w.gate, int, 1);
     A(w.xref, double, 3 * Nr);
     A(w.wshift, double, 3 * Nr);
@@ -449,6 +486,13 @@ d3_status plan_alloc(d3_handle* h, Plan& P) {
     P.w.offsets = doff;
     P.w.sid_in = dsid;
     P.w.fin_sid = dfin;
+    P.w.clu_sid = dclu;
+    P.w.ncl = ncl;
+    P.acc = w.acc;  // attached to the Work of cluster-mode calls only
+    P.vd = w.vd;
+    P.w.acc = nullptr;
+    P.w.vd = nullptr;
+    P.w.cl_mode = 0;
     const double rld = list_radius(h, h->prm.rc_disp_A), rln = list_radius(h, h->prm.rc_cn_A);
     w.rl_disp2 = (float)(rld * rld);
     w.rl_cn2 = (float)(rln * rln);
@@ -462,6 +506,8 @@ d3_status plan_alloc(d3_handle* h, Plan& P) {
     if (e == cudaSuccess && nfin > 0)
         e = cudaMemcpy(dfin, fin_sid.data(), sizeof(int) * (size_t)nfin, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(doff, P.offsets.data(), sizeof(int64_t) * (B + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && ncl > 0)
+        e = cudaMemcpy(dclu, clu_sid.data(), sizeof(int) * (size_t)ncl, cudaMemcpyHostToDevice);
     if (e == cudaSuccess && Nr > 0) {
         std::vector<int> sid((size_t)Nr);
         for (int s = 0; s < B; ++s)
@@ -535,8 +581,13 @@ std::array<int, 4> size_class(const d3_handle* h, const Plan& P) {
 // Enqueue the neighbour build.  gated (list reuse, skin > 0): a displacement
 // check first decides on the device whether the build runs; the sorted
 // positions are rewritten either way.
-d3_status enqueue_build(d3_handle* h, Plan& P, const double* pos, const int32_t* types, cudaStream_t st,
+d3_status enqueue_build(d3_handle* h, Plan& P, const double* pos, const int32_t* types, cudaStream_t st, int mode,
                         bool gated = false) {
+    // a build in the other list mode re-sorted the atoms: the first build in
+    // this mode must run whatever the displacement check would decide
+    if (P.last_mode != mode) gated = false;
+    set_mode(P, mode);
+    P.last_mode = mode;
     Work w = P.w;
     cudaError_t e = cudaSuccess;
     if (gated) {
@@ -548,7 +599,7 @@ d3_status enqueue_build(d3_handle* h, Plan& P, const double* pos, const int32_t*
     }
     e = launch_build_impl(w, pos, types, h->d_rk, P.bsum, st);
     if (e != cudaSuccess) return cuda_fail(h, e, "neighbour build launch");
-    if (P.Nr > 0) h->launches += kBuildLaunches;
+    if (P.Nr > 0) h->launches += kBuildLaunches + (mode == kClusterLists && P.ncl > 0 ? 1 : 0);
     return D3_OK;
 }
 
@@ -559,7 +610,7 @@ d3_status enqueue_build(d3_handle* h, Plan& P, const double* pos, const int32_t*
 // Each stage is timed with events on the caller's stream.  The runs write
 // only the plan's workspace and scratch outputs, and the device build counter
 // is put back afterwards.
-d3_status tune_shapes(d3_handle* h, Plan& P, const double* pos, const int32_t* types, cudaStream_t st) {
+d3_status tune_shapes(d3_handle* h, Plan& P, const double* pos, const int32_t* types, cudaStream_t st, int mode) {
     if (!h->autotune) return D3_OK;
     if (P.Nr < kTuneMinAtoms) {
         set_shapes(h, kDefaultShape);
@@ -591,6 +642,8 @@ d3_status tune_shapes(d3_handle* h, Plan& P, const double* pos, const int32_t* t
     c.accumulate = 0;
     const Tabs tb = forward_tabs(h);
     const bool mixed = h->prm.precision == D3_MIXED;
+    set_mode(P, mode);
+    P.last_mode = mode;
     Work w = P.w;
     // t[kernel][candidate]: build, CN, dispersion, chain
     float t[4][2];
@@ -605,7 +658,7 @@ d3_status tune_shapes(d3_handle* h, Plan& P, const double* pos, const int32_t* t
             if (e == cudaSuccess) e = launch_forward(w, c, mixed, tb, E, F, W, nullptr, nullptr, nullptr, P.B, st,
                                                      ev.data() + 1);
             if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-            h->launches += kBuildLaunches + kForwardLaunches + c.atm;
+            h->launches += kBuildLaunches + kForwardLaunches + c.atm + 2 * w.cl_mode;
             const int from[4] = {0, 1, 3, 5};
             for (int m = 0; m < 4 && e == cudaSuccess; ++m) {
                 float ms = 0.f;
@@ -635,12 +688,13 @@ d3_status tune_shapes(d3_handle* h, Plan& P, const double* pos, const int32_t* t
 // Make the plan match the geometry; on a new geometry run the build once
 // synchronously and grow image and list capacities until nothing overflows.
 d3_status ensure_plan(d3_handle* h, int32_t B, const int64_t* offsets, const double* pos, const int32_t* types,
-                      const double* cells, const int32_t* pbc, cudaStream_t st) {
+                      const double* cells, const int32_t* pbc, cudaStream_t st, int mode) {
     Plan& P = h->plan;
-    if (same_geometry(P, B, offsets, cells, pbc) && P.sized) return D3_OK;
+    if (same_geometry(P, B, offsets, cells, pbc) && P.sized[mode]) return D3_OK;
     if (!same_geometry(P, B, offsets, cells, pbc)) {
         P.valid = false;
-        P.sized = false;
+        P.sized[0] = P.sized[1] = false;
+        P.last_mode = -1;
         P.B = B;
         P.offsets.assign(offsets, offsets + B + 1);
         P.cells.assign(cells, cells + 9 * (size_t)B);
@@ -660,12 +714,12 @@ d3_status ensure_plan(d3_handle* h, int32_t B, const int64_t* offsets, const dou
     for (int attempt = 0; attempt < 4; ++attempt) {
         cudaError_t e = cudaMemsetAsync(h->d_status, 0, sizeof(int), st);
         if (e != cudaSuccess) return cuda_fail(h, e, "status reset");
-        d3_status s = enqueue_build(h, P, pos, types, st);
+        d3_status s = enqueue_build(h, P, pos, types, st, mode);
         if (s != D3_OK) return s;
         int gcount = 0, status = 0;
-        std::vector<int> mx(2 * (size_t)std::max(B, 1), 0);
+        std::vector<int> mx(3 * (size_t)std::max(B, 1), 0);
         e = cudaMemcpyAsync(&gcount, P.w.ghost_count, sizeof(int), cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess && B > 0) e = cudaMemcpyAsync(mx.data(), P.w.maxcnt, sizeof(int) * 2 * B, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && B > 0) e = cudaMemcpyAsync(mx.data(), P.w.maxcnt, sizeof(int) * 3 * B, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(&status, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return cuda_fail(h, e, "sizing pass");
@@ -678,13 +732,15 @@ d3_status ensure_plan(d3_handle* h, int32_t B, const int64_t* offsets, const dou
         }
         for (int s2 = 0; s2 < B; ++s2) {
             StructGeo& G = P.geo[s2];
-            if (mx[2 * s2] > G.cap_disp) { G.cap_disp = round_cap(mx[2 * s2] * 1.1 + 16); grow = true; }
-            if (mx[2 * s2 + 1] > G.cap_cn) { G.cap_cn = round_cap(mx[2 * s2 + 1] * 1.1 + 8); grow = true; }
+            if (mx[3 * s2] > G.cap_disp) { G.cap_disp = round_cap(mx[3 * s2] * 1.1 + 16); grow = true; }
+            if (mx[3 * s2 + 1] > G.cap_cn) { G.cap_cn = round_cap(mx[3 * s2 + 1] * 1.1 + 8); grow = true; }
+            if (mx[3 * s2 + 2] > G.cap_cl) { G.cap_cl = round_cap(mx[3 * s2 + 2] * 1.1 + 16); grow = true; }
         }
         if (!grow) {
-            P.sized = true;
-            return tune_shapes(h, P, pos, types, st);
+            P.sized[mode] = true;
+            return tune_shapes(h, P, pos, types, st, mode);
         }
+        P.sized[0] = P.sized[1] = false;  // the buffers are reallocated: both modes re-measure
         s = plan_alloc(h, P);
         if (s != D3_OK) return s;
     }
@@ -703,6 +759,12 @@ d3_status check_batch_args(d3_handle* h, int32_t B, const int64_t* offsets, cons
     return D3_OK;
 }
 
+// List mode of a forward call: cluster lists for the mixed form, full per-atom
+// lists for the FP64 form and for the per-atom virial of Eq. 7.
+int list_mode(const d3_handle* h, const double* w_atom) {
+    return h->prm.precision == D3_MIXED && !w_atom ? kClusterLists : kFullLists;
+}
+
 d3_status forward(d3_handle* h, int32_t B, const int64_t* offsets, const double* pos, const int32_t* types,
                   const double* cells, const int32_t* pbc, double* E, double* F, double* W, double* e_atom,
                   double* cn, cudaStream_t st, double* w_atom = nullptr) {
@@ -715,7 +777,8 @@ d3_status forward(d3_handle* h, int32_t B, const int64_t* offsets, const double*
                                    "disable the three-body term");
     h->last_stream = st;
     if (B == 0) return D3_OK;
-    s = ensure_plan(h, B, offsets, pos, types, cells, pbc, st);
+    const int mode = list_mode(h, w_atom);
+    s = ensure_plan(h, B, offsets, pos, types, cells, pbc, st, mode);
     if (s != D3_OK) return s;
     Plan& P = h->plan;
     std::vector<cudaEvent_t> ev;
@@ -723,7 +786,7 @@ d3_status forward(d3_handle* h, int32_t B, const int64_t* offsets, const double*
         ev = take_events(h, kStages + 1);
         if (ev.size() == kStages + 1) cudaEventRecord(ev[0], st);
     }
-    s = enqueue_build(h, P, pos, types, st, h->prm.skin_A > 0);
+    s = enqueue_build(h, P, pos, types, st, mode, h->prm.skin_A > 0);
     if (s != D3_OK) return s;
     const Consts c = make_consts(h);
     const bool mixed = h->prm.precision == D3_MIXED;
@@ -731,7 +794,7 @@ d3_status forward(d3_handle* h, int32_t B, const int64_t* offsets, const double*
     cudaError_t e = launch_forward(P.w, c, mixed, tb, E, F, W, e_atom, cn, w_atom, B, st,
                                    ev.size() == kStages + 1 ? ev.data() + 1 : nullptr);
     if (e != cudaSuccess) return cuda_fail(h, e, "forward launch");
-    h->launches += (P.Nr > 0 ? kForwardLaunches + c.atm : 1);
+    h->launches += (P.Nr > 0 ? kForwardLaunches + c.atm + (mode == kClusterLists ? 1 : 0) : 1);
     if (ev.size() == kStages + 1) h->ev_pending.push_back(ev);
     else for (cudaEvent_t x : ev) h->ev_pool.push_back(x);
     return D3_OK;
@@ -760,9 +823,14 @@ d3_status forward_graph(d3_handle* h, int32_t B, const int64_t* offsets, const d
     d3_status s = check_batch_args(h, B, offsets, pos, types, cells, pbc);
     if (s != D3_OK) return s;
     if (!E || !W || !F) return fail(h, D3_ERR_ARG, "NULL E, F or W");
-    s = ensure_plan(h, B, offsets, pos, types, cells, pbc, st);
+    const int mode = list_mode(h, w_atom);
+    s = ensure_plan(h, B, offsets, pos, types, cells, pbc, st, mode);
     if (s != D3_OK) return s;
     h->last_stream = st;
+    // the last build was in the other list mode: rebuild once directly (a
+    // replayed graph would take the list-reuse decision on stale lists)
+    if (h->plan.last_mode != mode)
+        return forward(h, B, offsets, pos, types, cells, pbc, E, F, W, e_atom, cn, st, w_atom);
     const void* key[10] = {pos, types, E, F, W, e_atom, cn, w_atom, (const void*)(intptr_t)h->plan_gen,
                            (const void*)(intptr_t)(h->param_gen * 2 + (h->accumulate ? 1 : 0))};
     if (!graph_key_match(h, key)) {
@@ -1012,9 +1080,10 @@ d3_status d3_build_neighbors(d3_handle* h, int32_t B, const int64_t* offsets, co
     cudaStream_t st = (cudaStream_t)stream;
     h->last_stream = st;
     if (B == 0) return D3_OK;
-    s = ensure_plan(h, B, offsets, pos, types, cells, pbc, st);
+    const int mode = list_mode(h, nullptr);
+    s = ensure_plan(h, B, offsets, pos, types, cells, pbc, st, mode);
     if (s != D3_OK) return s;
-    s = enqueue_build(h, h->plan, pos, types, st);
+    s = enqueue_build(h, h->plan, pos, types, st, mode);
     if (s != D3_OK) return s;
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(h, e, "build");
@@ -1109,10 +1178,10 @@ d3_status d3_backward(d3_handle* h, int32_t B, const int64_t* offsets, const dou
         }
         return D3_OK;
     }
-    s = ensure_plan(h, B, offsets, pos, types, cells, pbc, st);
+    s = ensure_plan(h, B, offsets, pos, types, cells, pbc, st, kFullLists);
     if (s != D3_OK) return s;
     Plan& P = h->plan;
-    s = enqueue_build(h, P, pos, types, st);
+    s = enqueue_build(h, P, pos, types, st, kFullLists);
     if (s != D3_OK) return s;
     const int64_t need = backward_scratch_doubles(P.w, B);
     if (need > P.bwd_scratch_n) {
@@ -1148,8 +1217,11 @@ d3_status d3_sync_status(d3_handle* h) {
     if (st & ST_TYPE) return fail(h, D3_ERR_TYPE, "atom type out of range");
     if (st & ST_RANGE)
         return fail(h, D3_ERR_ARG, "a coordinate lies beyond the supported range (|x| < 4200 A after wrapping)");
+    if (st & ST_SUM_RANGE)
+        return fail(h, D3_ERR_ARG, "a dispersion partial sum exceeded its fixed-point range (|sum| < 2^23 Hartree "
+                                   "or Hartree/bohr): the damping parameters or reference data are out of range");
     if (st & (ST_GHOST_CAP | ST_LIST_CAP)) {
-        h->plan.sized = false;  // the next call re-measures and regrows
+        h->plan.sized[0] = h->plan.sized[1] = false;  // the next call re-measures and regrows
         return fail(h, D3_ERR_CAPACITY, "neighbour or image capacity exceeded; buffers will be regrown");
     }
     h->err.clear();

@@ -7,10 +7,12 @@
 //     also covers a margin of one list radius around the cell,
 //   * explicit image atoms ("ghosts") for every periodic image that falls in
 //     that margin, so the pair kernels never apply lattice translations,
-//   * a counting sort of real atoms and of image atoms by cell (stable: each
-//     cell is re-sorted by source index, so the order is deterministic),
+//   * a counting sort of real atoms and of image atoms by cell (serpentine
+//     cell numbering; each cell is re-sorted by a deterministic key),
 //   * FP64 and split-FP32 (hi + lo) positions of every atom in sorted order,
-//   * per-atom neighbour lists within the two list radii.
+//   * per-atom neighbour lists within the two list radii, or (cluster mode)
+//     per-atom lists within the CN radius and, for the dispersion pass,
+//     half lists per cluster of 8 consecutive sorted atoms.
 // Every kernel writes only inside the capacities it is given and records an
 // overflow in the status word instead.
 #include <algorithm>
@@ -30,15 +32,25 @@ __device__ __forceinline__ bool skip_build(const Work& w) { return w.gate && *w.
 // bohr), so an atom binned one cell off, or an image kept or dropped at the
 // edge of its window, changes no pair within the cutoffs.  Positions
 // themselves stay FP64.
-__device__ inline int cell_id(const StructGeo& G, const float f[3]) {
+// Cell of a fractional position (serpentine numbering, cell_index); *fx is the
+// position along the cell's row in the direction the numbering runs, the key
+// that orders atoms inside a cell.
+__device__ inline int cell_id(const StructGeo& G, const float f[3], float* fx = nullptr) {
     int c[3];
+    float u0 = 0.0f;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         float u = (f[k] - G.lof[k]) * G.fscalef[k];
         u = fminf(fmaxf(u, 0.0f), (float)(G.ncell[k] - 1));
+        if (k == 0) u0 = u;
         c[k] = (int)u;
     }
-    return (int)(G.cell_base + ((int64_t)c[2] * G.ncell[1] + c[1]) * G.ncell[0] + c[0]);
+    const int64_t id = cell_index(G, c[0], c[1], c[2]);
+    if (fx) {
+        const int64_t row = (id - G.cell_base) / G.ncell[0];
+        *fx = (row & 1) ? -u0 : u0;
+    }
+    return (int)id;
 }
 
 __device__ __forceinline__ bool finite_bits(double x) {
@@ -123,8 +135,10 @@ __global__ void __launch_bounds__(256) k_wrap(Work w, const double* __restrict__
             w.wshift[3 * i + a] = xw[a] - xb[a];
         }
     }
-    const int cid = cell_id(G, f);
+    float key;
+    const int cid = cell_id(G, f, &key);
     w.cell_of[i] = cid;
+    w.skey[i] = key;
     w.slot_of[i] = atomicAdd(&w.cnt_real[cid], 1);
     // occupied range: one atomic per group of lanes in the same structure
     const unsigned grp = __match_any_sync(__activemask(), s);
@@ -213,7 +227,7 @@ __global__ void __launch_bounds__(256) k_images(Work w) {
                     return;
                 }
                 const int cz = cell_of_axis(2, n2);
-                const int gc = (int)(G.cell_base + ((int64_t)cz * G.ncell[1] + cy) * G.ncell[0] + cx);
+                const int gc = (int)cell_index(G, cx, cy, cz);
                 w.ghost_src[slot] = (int)i;
                 w.ghost_shift[slot] = pack_shift(n0, n1, n2);
                 w.ghost_cell[slot] = gc;
@@ -303,8 +317,10 @@ __global__ void k_scatter_ghost(Work w) {
     w.gsorted[w.start_ghost[w.ghost_cell[g]] + w.ghost_slot[g]] = g;
 }
 
-// Deterministic order inside each cell: real atoms by input index, images by
-// (source, translation).  A block takes 256 consecutive cells, whose atoms
+// Deterministic order inside each cell: real atoms by their position along the
+// cell's row in the direction the serpentine numbering runs (ties by input
+// index), so that runs of consecutive sorted atoms, the clusters of the
+// dispersion pass, are compact; images by (source, translation).  A block takes 256 consecutive cells, whose atoms
 // form one contiguous slice of sorted slots: the slice is staged in shared
 // memory, each thread insertion-sorts its own cell there, and the slice is
 // written back.  A slice larger than the stage is sorted in place in global
@@ -313,6 +329,14 @@ constexpr int kSortStage = 2048;
 
 __device__ __forceinline__ long long image_key(const Work& w, int g) {
     return ((long long)w.ghost_src[g] << 24) | (long long)w.ghost_shift[g];
+}
+// order-preserving map of a float to an unsigned int
+__device__ __forceinline__ unsigned float_order(float x) {
+    const unsigned b = __float_as_uint(x);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ long long real_key(const Work& w, int i) {
+    return (long long)(((unsigned long long)float_order(w.skey[i]) << 32) | (unsigned)i);
 }
 
 __global__ void __launch_bounds__(256) k_sort_cells(Work w) {
@@ -328,26 +352,46 @@ __global__ void __launch_bounds__(256) k_sort_cells(Work w) {
         const int lo = w.start_real[c0], hi = w.start_real[c1];
         const bool fits = hi - lo <= kSortStage;
         if (fits)
-            for (int k = lo + threadIdx.x; k < hi; k += blockDim.x) sr[k - lo] = w.sorted_src[k];
+            for (int k = lo + threadIdx.x; k < hi; k += blockDim.x) {
+                const int i = w.sorted_src[k];
+                sr[k - lo] = i;
+                sk[k - lo] = real_key(w, i);
+            }
         __syncthreads();
         if (live) {
             const int b = w.start_real[c], e = w.start_real[c + 1];
-            // slots [b, e) of the cell: in the stage at [b - lo, e - lo), else in place
-            int* v = fits ? sr : w.sorted_src;
-            const int o = fits ? lo : 0;
-            for (int k = b + 1 - o; k < e - o; ++k) {
-                const int key = v[k];
-                int m = k - 1;
-                while (m >= b - o && v[m] > key) {
-                    v[m + 1] = v[m];
-                    --m;
+            if (fits) {
+                for (int k = b + 1 - lo; k < e - lo; ++k) {
+                    const int i = sr[k];
+                    const long long key = sk[k];
+                    int m = k - 1;
+                    while (m >= b - lo && sk[m] > key) {
+                        sk[m + 1] = sk[m];
+                        sr[m + 1] = sr[m];
+                        --m;
+                    }
+                    sk[m + 1] = key;
+                    sr[m + 1] = i;
                 }
-                v[m + 1] = key;
+            } else {
+                for (int k = b + 1; k < e; ++k) {
+                    const int i = w.sorted_src[k];
+                    const long long key = real_key(w, i);
+                    int m = k - 1;
+                    while (m >= b) {
+                        const int h = w.sorted_src[m];
+                        if (real_key(w, h) <= key) break;
+                        w.sorted_src[m + 1] = h;
+                        --m;
+                    }
+                    w.sorted_src[m + 1] = i;
+                }
             }
         }
         __syncthreads();
         if (fits)
             for (int k = lo + threadIdx.x; k < hi; k += blockDim.x) w.sorted_src[k] = sr[k - lo];
+        __syncthreads();  // sk is reused for the images below
     }
     {
         const int lo = w.start_ghost[c0], hi = w.start_ghost[c1];
@@ -403,7 +447,7 @@ __global__ void k_reset(Work w) {
         w.cnt_real[k] = 0;
         w.cnt_ghost[k] = 0;
     }
-    if (k < 2 * (int64_t)w.B) w.maxcnt[k] = 0;
+    if (k < 3 * (int64_t)w.B) w.maxcnt[k] = 0;
     // occupied-range minima start at a huge float, maxima at +0
     if (k < 3 * (int64_t)w.B) {
         w.frange[k] = 0x7f7f7f7f;
@@ -411,7 +455,8 @@ __global__ void k_reset(Work w) {
     }
     if (k == 0) {
         *w.ghost_count = 0;
-        *w.work_ctr = 0;
+        w.work_ctr[0] = 0;
+        w.work_ctr[1] = 0;
         atomicAdd(w.nbuild, 1ull);
     }
 }
@@ -458,7 +503,7 @@ __device__ inline void store_pos(Work& w, int64_t q, const double x[3], double r
     }
     w.rec[2 * q] = make_float4(h[0], h[1], h[2], __int_as_float(tsrc));
     w.rec[2 * q + 1] = make_float4(l[0], l[1], l[2], (float)rk);
-    w.hi[q] = make_float4(h[0], h[1], h[2], 0.f);
+    w.hi[q] = make_float4(h[0], h[1], h[2], __int_as_float(tsrc));
 }
 
 __global__ void k_fill_real(Work w, const int32_t* __restrict__ types, const double* __restrict__ rk_tab) {
@@ -509,14 +554,14 @@ __global__ void k_fill_ghost(Work w, const int32_t* __restrict__ types, const do
     const int tsrc = t | (ps << 4);
     w.rec[2 * (w.Nr + q)] = make_float4(h[0], h[1], h[2], __int_as_float(tsrc));
     w.rec[2 * (w.Nr + q) + 1] = make_float4(l[0], l[1], l[2], ls.w);
-    w.hi[w.Nr + q] = make_float4(h[0], h[1], h[2], 0.f);
+    w.hi[w.Nr + q] = make_float4(h[0], h[1], h[2], __int_as_float(tsrc));
 }
 
 // ---- per-atom lists within the two list radii ------------------------------
 // Positions used here are the grid-aligned hi parts (error <= sqrt(3) 2^-10
-// bohr, covered by the list margin).  Both variants are persistent: each warp
-// repeatedly takes the next 32 consecutive sorted atoms from a global counter,
-// which balances uneven chunks across SMs.
+// bohr, covered by the list margin).  Both builders are persistent: each warp
+// repeatedly takes the next piece of work from a global counter, which
+// balances uneven structures across SMs.
 
 // Shared per-atom state of a list builder lane.
 struct ListLane {
@@ -541,11 +586,7 @@ struct ListLane {
         capd = capc = nd = nc = 0;
         if (!live) return;
         const StructGeo& G = w.geo[s];
-        int rel = w.cell_sorted[P] - (int)G.cell_base;
-        c0 = rel % G.ncell[0];
-        rel /= G.ncell[0];
-        c1 = rel % G.ncell[1];
-        c2 = rel / G.ncell[1];
+        cell_coords(G, w.cell_sorted[P], c0, c1, c2);
         hp = rec_hi(w, P);
         const int64_t local = P - G.atom_base;
         Ld = w.nbr_disp + list_row(G.list_base_disp, local, G.cap_disp);
@@ -578,8 +619,8 @@ struct ListLane {
     __device__ void finish(Work& w, int lane) {
         if (live) {
             drain(Ld, capd, nd, bd);
-            drain(Lc, capc, nc, bc);
             w.cnt_disp[p] = min(nd, capd);
+            drain(Lc, capc, nc, bc);
             w.cnt_cn[p] = min(nc, capc);
             if (nd > capd || nc > capc) atomicOr(w.status, ST_LIST_CAP);
         }
@@ -587,16 +628,16 @@ struct ListLane {
         const unsigned grp = __match_any_sync(0xffffffffu, s);
         const int md = __reduce_max_sync(grp, nd), mc = __reduce_max_sync(grp, nc);
         if (live && lane == __ffs(grp) - 1) {
-            atomicMax(&w.maxcnt[2 * s], md);
-            atomicMax(&w.maxcnt[2 * s + 1], mc);
+            atomicMax(&w.maxcnt[3 * s], md);
+            atomicMax(&w.maxcnt[3 * s + 1], mc);
         }
     }
 };
 
-__device__ __forceinline__ int64_t next_chunk(const Work& w, int lane) {
+__device__ __forceinline__ int64_t next_chunk(const Work& w, int lane, int ctr) {
     int chunk = 0;
-    if (lane == 0) chunk = atomicAdd(w.work_ctr, 1);
-    return (int64_t)__shfl_sync(0xffffffffu, chunk, 0) * 32;
+    if (lane == 0) chunk = atomicAdd(w.work_ctr + ctr, 1);
+    return (int64_t)__shfl_sync(0xffffffffu, chunk, 0);
 }
 
 // Every thread walks the cell window of its own atom, rows of cells as
@@ -609,7 +650,7 @@ __global__ void __launch_bounds__(128) k_build_lists(Work w) {
     const float4* __restrict__ H = w.hi;
     __shared__ __align__(16) int stage[2][128][8];
     for (;;) {
-        const int64_t p0 = next_chunk(w, lane);
+        const int64_t p0 = next_chunk(w, lane, 0) * 32;
         if (p0 >= w.Nr) return;
         ListLane L;
         L.init(w, p0 + lane, stage[0][threadIdx.x], stage[1][threadIdx.x]);
@@ -625,10 +666,11 @@ __global__ void __launch_bounds__(128) k_build_lists(Work w) {
             };
             for (int z = z0; z <= z1; ++z)
                 for (int y = y0; y <= y1; ++y) {
-                    const int64_t row = G.cell_base + ((int64_t)z * G.ncell[1] + y) * G.ncell[0];
-                    const int rb = __ldg(&w.start_real[row + x0]), re = __ldg(&w.start_real[row + x1 + 1]);
-                    const int gb = (int)w.Nr + __ldg(&w.start_ghost[row + x0]);
-                    const int ge = (int)w.Nr + __ldg(&w.start_ghost[row + x1 + 1]);
+                    int64_t cf, cl;
+                    row_cells(G, y, z, x0, x1, cf, cl);
+                    const int rb = __ldg(&w.start_real[cf]), re = __ldg(&w.start_real[cl + 1]);
+                    const int gb = (int)w.Nr + __ldg(&w.start_ghost[cf]);
+                    const int ge = (int)w.Nr + __ldg(&w.start_ghost[cl + 1]);
                     for (int pass = 0; pass < 2; ++pass) {
                         const int b = pass == 0 ? rb : gb, e = pass == 0 ? re : ge;
                         int u = b;
@@ -645,6 +687,164 @@ __global__ void __launch_bounds__(128) k_build_lists(Work w) {
                 }
         }
         L.finish(w, lane);
+    }
+}
+
+// ---- cluster lists of the dispersion pass ---------------------------------
+// Cluster I of structure s is the run of sorted real atoms
+// [atom_base + 8 (I - clu_base), + 8) (fewer at the end of a structure).  Its
+// list holds every atom q, real or image, whose hi position lies within the
+// list radius of the cluster's bounding box and that the half rule assigns to
+// I: each unordered pair instance of Eq. 2 must be listed exactly once.  With
+// src the source real atom of q and n its lattice translation:
+//   src in a later cluster                       listed (here, not there)
+//   src in an earlier cluster                    not listed (listed there)
+//   src in I, q real                             listed; the pass keeps only q > i
+//   src in I, q an image                         listed when n > 0 (packed order):
+//                                                (i, src, n) and (src, i, -n) are one instance
+// The same walk writes the per-atom CN lists of the cluster's atoms (every
+// atom within the CN list radius of each, both directions).
+// One warp per cluster walks the union of its atoms' cell windows.  The rows
+// of cells (real and image atoms of each row: two index ranges per row) are
+// flattened: 32 ranges at a time, their lengths scanned across the lanes, then
+// 32 candidates at a time, each lane finding its range by a binary search over
+// the scanned offsets held in the lanes.  Candidates are appended in walk
+// order (ballot compaction), so every list is deterministic.
+__global__ void __launch_bounds__(128) k_build_clist(Work w) {
+    if (skip_build(w)) return;
+    const int lane = threadIdx.x & 31;
+    const unsigned full = 0xffffffffu;
+    const float rd2 = w.rl_disp2, rn2 = w.rl_cn2;
+    const float4* __restrict__ H = w.hi;
+    const int zero_shift = pack_shift(0, 0, 0);
+    __shared__ float4 sh_i[4][kClusterAtoms];  // the cluster's atoms (hi positions) per warp
+    float4* hi8 = sh_i[threadIdx.x >> 5];
+    for (;;) {
+        const int64_t I = next_chunk(w, lane, 1);
+        if (I >= w.ncl) return;
+        const int s = w.clu_sid[I];
+        const StructGeo& G = w.geo[s];
+        const int64_t p0 = G.atom_base + (I - G.clu_base) * kClusterAtoms;
+        const int64_t rem = G.atom_base + G.natoms - p0;
+        const int nI = rem < kClusterAtoms ? (int)rem : kClusterAtoms;
+        // bounding box (hi positions) and cell range of the cluster's atoms
+        const bool own = lane < nI;
+        const float4 h = __ldg(&H[own ? p0 + lane : p0]);
+        if (lane < kClusterAtoms) hi8[lane] = h;
+        int cx, cy, cz;
+        cell_coords(G, w.cell_sorted[own ? p0 + lane : p0], cx, cy, cz);
+        float lo[3] = {h.x, h.y, h.z}, hi[3] = {h.x, h.y, h.z};
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                lo[k] = fminf(lo[k], __shfl_xor_sync(full, lo[k], o));
+                hi[k] = fmaxf(hi[k], __shfl_xor_sync(full, hi[k], o));
+            }
+        __syncwarp();
+        const int x0 = max(0, __reduce_min_sync(full, cx) - G.win[0]);
+        const int x1 = min(G.ncell[0] - 1, __reduce_max_sync(full, cx) + G.win[0]);
+        const int y0 = max(0, __reduce_min_sync(full, cy) - G.win[1]);
+        const int y1 = min(G.ncell[1] - 1, __reduce_max_sync(full, cy) + G.win[1]);
+        const int z0 = max(0, __reduce_min_sync(full, cz) - G.win[2]);
+        const int z1 = min(G.ncell[2] - 1, __reduce_max_sync(full, cz) + G.win[2]);
+        const int ny = y1 - y0 + 1, nranges = 2 * ny * (z1 - z0 + 1);
+        int* row = w.nbr_cl + G.list_base_cl + (I - G.clu_base) * (int64_t)G.cap_cl;
+        const int cap = G.cap_cl, capc = G.cap_cn;
+        const int first = (int)p0, last = (int)p0 + nI;  // the cluster's own sorted slots
+        int n = 0;
+        int nc[kClusterAtoms] = {0, 0, 0, 0, 0, 0, 0, 0};  // CN list lengths (warp-uniform)
+        for (int r0 = 0; r0 < nranges; r0 += 32) {
+            // this lane's range: row (y, z) = (r / 2) and real (r even) or image atoms
+            int b = 0, len = 0;
+            const int r = r0 + lane;
+            if (r < nranges) {
+                const int rr = r >> 1;
+                const int y = y0 + rr % ny, z = z0 + rr / ny;
+                int64_t cf, cl;
+                row_cells(G, y, z, x0, x1, cf, cl);
+                if ((r & 1) == 0) {
+                    b = __ldg(&w.start_real[cf]);
+                    len = __ldg(&w.start_real[cl + 1]) - b;
+                } else {
+                    b = (int)w.Nr + __ldg(&w.start_ghost[cf]);
+                    len = (int)w.Nr + __ldg(&w.start_ghost[cl + 1]) - b;
+                }
+            }
+            int incl = len;  // inclusive scan of the lengths over the lanes
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(full, incl, o);
+                if (lane >= o) incl += v;
+            }
+            const int excl = incl - len;
+            const int total = __shfl_sync(full, incl, 31);
+            for (int f0 = 0; f0 < total; f0 += 32) {
+                const int f = f0 + lane;
+                // the range holding flat candidate f: the last lane k with excl_k <= f
+                int k = 0;
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1) {
+                    const int e = __shfl_sync(full, excl, k + step);
+                    if (e <= f) k += step;
+                }
+                const int q = __shfl_sync(full, b, k) + (f - __shfl_sync(full, excl, k));
+                const bool img = ((r0 + k) & 1) != 0;
+                bool take = false, cn_cand = false;
+                float4 hq = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (f < total) {
+                    hq = __ldg(&H[q]);
+                    const float gx = fmaxf(0.0f, fmaxf(lo[0] - hq.x, hq.x - hi[0]));
+                    const float gy = fmaxf(0.0f, fmaxf(lo[1] - hq.y, hq.y - hi[1]));
+                    const float gz = fmaxf(0.0f, fmaxf(lo[2] - hq.z, hq.z - hi[2]));
+                    const float g2 = fmaf(gx, gx, fmaf(gy, gy, gz * gz));
+                    cn_cand = g2 < rn2;
+                    if (g2 < rd2) {
+                        const int src = __float_as_int(hq.w) >> 4;
+                        if (src >= last) {
+                            take = true;
+                        } else if (src >= first) {
+                            take = !img || w.ghost_shift[w.gsorted[q - (int)w.Nr]] > zero_shift;
+                        }
+                    }
+                }
+                const unsigned m = __ballot_sync(full, take);
+                const int kk = n + __popc(m & ((1u << lane) - 1u));
+                if (take && kk < cap) row[kk] = q;
+                n += __popc(m);
+                // per-atom CN lists of the cluster's atoms
+                if (__any_sync(full, cn_cand)) {
+#pragma unroll
+                    for (int i = 0; i < kClusterAtoms; ++i) {
+                        if (i >= nI) break;
+                        const float4 hp = hi8[i];
+                        const float dx = hq.x - hp.x, dy = hq.y - hp.y, dz = hq.z - hp.z;
+                        const bool in = cn_cand && q != first + i && fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < rn2;
+                        const unsigned mi = __ballot_sync(full, in);
+                        if (mi) {
+                            const int kc = nc[i] + __popc(mi & ((1u << lane) - 1u));
+                            if (in && kc < capc)
+                                w.nbr_cn[list_row(G.list_base_cn, (int64_t)first + i - G.atom_base, capc) + kc] = q;
+                            nc[i] += __popc(mi);
+                        }
+                    }
+                }
+            }
+        }
+        int mc = 0;
+#pragma unroll
+        for (int i = 0; i < kClusterAtoms; ++i)
+            if (i < nI) {
+                mc = max(mc, nc[i]);
+                if (lane == i) w.cnt_cn[first + i] = min(nc[i], capc);
+            }
+        if (lane == 0) {
+            w.cnt_cl[I] = min(n, cap);
+            if (n > cap || mc > capc) atomicOr(w.status, ST_LIST_CAP);
+            atomicMax(&w.maxcnt[3 * s + 2], n);
+            atomicMax(&w.maxcnt[3 * s + 1], mc);
+        }
+        __syncwarp();
     }
 }
 
@@ -683,9 +883,15 @@ cudaError_t launch_build_impl(const Work& w, const double* pos, const int32_t* t
     if (w.ghost_cap > 0) k_fill_ghost<<<nblk(w.ghost_cap, TB), TB, 0, st>>>(w, types, rk_tab);
     {
         // persistent warps: w.build_per_sm blocks per SM, work handed out per 32 atoms
+        // (per-atom lists) and per cluster (cluster lists)
         const int chunks = (int)((w.Nr + 31) / 32);
         const int blocks = std::min((chunks + 3) / 4, w.num_sms * w.build_per_sm);
-        k_build_lists<<<blocks, 128, 0, st>>>(w);
+        if (w.cl_mode) {  // cluster lists and, in the same walk, the per-atom CN lists
+            const int bcl = (int)std::min<int64_t>((w.ncl + 3) / 4, (int64_t)w.num_sms * w.build_per_sm);
+            if (w.ncl > 0) k_build_clist<<<bcl, 128, 0, st>>>(w);
+        } else {
+            k_build_lists<<<blocks, 128, 0, st>>>(w);
+        }
     }
     return cudaGetLastError();
 }

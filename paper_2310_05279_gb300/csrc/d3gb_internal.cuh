@@ -41,6 +41,7 @@ enum StatusBits : int {
     ST_NONFINITE = 4,
     ST_TYPE = 8,
     ST_RANGE = 16,  // a wrapped coordinate beyond kMaxCoordBohr
+    ST_SUM_RANGE = 32,  // a partial sum of the cluster-list dispersion pass beyond its fixed-point range
 };
 // Largest |coordinate| (bohr) after wrapping: the 2^-10 bohr grid split of a
 // position is exact in FP32 below 2^13 bohr; the rest is margin for images.
@@ -59,17 +60,49 @@ struct StructGeo {
     // lattice rows split like positions: Hh on the 2^-10 bohr grid, Hl = H - Hh (FP32)
     float Hh[9], Hl[9];
     int ncell[3];
-    int win[3];       // window half-width (cells) covering the list radius
+    int win[3];       // window half-width (cells) covering the list radii
     int img[3];       // image range, 0 along open axes
     int pbc[3];
     int64_t cell_base;
     int64_t atom_base;
     int32_t natoms;
     int32_t cap_disp, cap_cn;
-    int32_t pad;
+    int32_t cap_cl;     // entries per row of the cluster lists
     int64_t fin_base;   // first chunk of the structure in the per-structure sums
     int64_t list_base_disp, list_base_cn;
+    int64_t clu_base;     // first cluster of the structure
+    int64_t list_base_cl;  // first entry of the structure's cluster-list rows
 };
+
+// Cells are numbered in serpentine order within a structure: planes along z,
+// rows along y in alternating direction from plane to plane, cells along x in
+// alternating direction from row to row, so that consecutive cells are always
+// neighbours and runs of consecutive sorted atoms stay compact.  A row of cells
+// (fixed y, z) is still one contiguous range of ids.
+__host__ __device__ inline int64_t cell_index(const StructGeo& G, int cx, int cy, int cz) {
+    const int yy = (cz & 1) ? G.ncell[1] - 1 - cy : cy;
+    const int64_t row = (int64_t)cz * G.ncell[1] + yy;
+    const int xx = (row & 1) ? G.ncell[0] - 1 - cx : cx;
+    return G.cell_base + row * G.ncell[0] + xx;
+}
+__host__ __device__ inline void cell_coords(const StructGeo& G, int64_t id, int& cx, int& cy, int& cz) {
+    const int64_t rel = id - G.cell_base;
+    const int64_t row = rel / G.ncell[0];
+    const int xx = (int)(rel - row * G.ncell[0]);
+    cz = (int)(row / G.ncell[1]);
+    const int yy = (int)(row - (int64_t)cz * G.ncell[1]);
+    cy = (cz & 1) ? G.ncell[1] - 1 - yy : yy;
+    cx = (row & 1) ? G.ncell[0] - 1 - xx : xx;
+}
+// first and last cell id of cells x0..x1 of row (cy, cz)
+__host__ __device__ inline void row_cells(const StructGeo& G, int cy, int cz, int x0, int x1, int64_t& first,
+                                          int64_t& last) {
+    const int64_t a = cell_index(G, x0, cy, cz), b = cell_index(G, x1, cy, cz);
+    first = a < b ? a : b;
+    last = a < b ? b : a;
+}
+// Atoms per cluster of the cluster lists (consecutive sorted real atoms of a structure).
+constexpr int kClusterAtoms = 8;
 
 // Pointers and sizes of one plan's workspace, passed by value to kernels.
 struct Work {
@@ -111,8 +144,18 @@ struct Work {
     int* nbr_cn;
     int* cnt_disp;           // [Nr]
     int* cnt_cn;             // [Nr]
-    int* maxcnt;             // [2*B] max list length per structure (disp, cn)
-    int* work_ctr;           // [1] persistent-kernel work counter (zeroed before each build)
+    int* maxcnt;             // [3*B] max list length per structure (disp, cn, cluster)
+    int* work_ctr;           // [2] persistent-kernel work counters (zeroed before each build)
+    // cluster lists of the dispersion pass (mixed form)
+    int cl_mode;             // build: 1 = CN per-atom lists and cluster lists, 0 = both per-atom lists
+    int64_t ncl;             // clusters over the batch
+    const int* clu_sid;      // [ncl] structure of each cluster
+    int* nbr_cl;             // rows of cap_cl entries per cluster
+    int* cnt_cl;             // [ncl]
+    unsigned long long* acc; // [Nr][8] fixed-point sums of the dispersion pass: F (3), dE/dn, site energy
+    float* vd;               // [Nr + ghost_cap][T][2][RP] per atom q (images included, copied from their
+                             // source) and partner type t: v_q^(t) and dv_q^(t)_a = sum_b C6ref[t][tq][a][b] dW_qb
+    float* skey;             // [Nr] within-cell sort key (position along the serpentine direction), input order
     // list reuse (skin > 0): the build kernels run only while *gate != 0
     int* gate;               // nullptr: unconditional build; else set by k_check when an atom moved > skin/2
     double* xref;            // [Nr*3] positions (bohr, input order) at the last build
@@ -144,6 +187,7 @@ struct Work {
 // Per-handle constants of the pair arithmetic.
 struct Consts {
     double rc_disp2, rc_cn2;   // bohr^2
+    float rc_disp2f;           // FP32 copy for the mixed form
     double k1, k3;
     double s6, s8, a1, a2;     // damping of Eq. 2 (a2 in bohr)
     int T, R, RP;
@@ -241,13 +285,18 @@ struct Tabs {
 cudaError_t launch_forward(const Work& w, const Consts& c, bool mixed, const Tabs& tabs, double* E, double* F,
                            double* W, double* e_atom, double* cn_out, double* w_atom, int B, cudaStream_t st,
                            cudaEvent_t* marks);
+// Dispersion pass of the mixed form over the cluster lists (d3gb_cluster.cu):
+// fills w.Fd, w.dEdn, w.eat and w.wv like the per-atom-list pass (with site =
+// false, w.eat holds per-cluster sums on each cluster's first atom instead of
+// site energies).
+cudaError_t launch_disp_cl(const Work& w, const Consts& c, const void* pair_tab, bool site, cudaStream_t st);
 // Optional three-body pass (d3gb_atm.cu): adds into w.eat, w.wv, w.Fd and
 // w.dEdn after the dispersion pass; rtab as Tabs::rtab in the handle's precision.
 cudaError_t launch_atm(const Work& w, const Consts& c, bool mixed, const void* rtab, cudaStream_t st);
 // Eq. 8 per atom: J_i = W_i . v_i (device arrays).
 cudaError_t launch_heat(int64_t n, const double* w_atom, const double* vel, double* J, cudaStream_t st);
 constexpr int kForwardLaunches = 5;  // kernels per forward pass (B > 0, N > 0): CN, dispersion, chain, 2 sums
-                                     // (one more with the three-body term)
+                                     // (one more with the three-body term, one more in cluster mode)
 constexpr int kBuildLaunches = 15;   // kernels per neighbour build (N > 0): reset, wrap, images, 2 x 3 scan,
-                                     // 2 scatter, sort, 2 fill, lists
+                                     // 2 scatter, sort, 2 fill, lists (one more in cluster mode)
 }  // namespace d3gb

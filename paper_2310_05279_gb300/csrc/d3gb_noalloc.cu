@@ -1,15 +1,19 @@
 // d3gb_noalloc.cu -- per-structure energy sums for callers that cannot allocate.
 //
-// Some callers cannot call cudaMalloc: code that runs while a CUDA stream is
-// being captured into a graph (allocation is not a capturable operation), host
-// programs that hand this library a fixed device-memory budget owned by their
-// own pool, and time-critical loops that cannot afford the implicit device
-// synchronisation an allocation may cause.  d3_structure_energies_noalloc
-// gives them the per-structure reduction of site energies with no allocation
-// at all: its scratch (a copy of the offsets, one partial sum per chunk of
-// atoms, and one completion counter per structure) lives in the file-scope
-// array below, which every GPU that loads the library holds until the process
-// exits.
+// Some callers cannot call cudaMalloc: host programs that keep all device
+// memory in their own pool and hand a library only the buffers they own, and
+// time-critical loops that cannot afford the implicit device synchronisation
+// an allocation may cause.  d3_structure_energies_noalloc gives them the
+// per-structure reduction of site energies with no allocation at all: its
+// scratch (a copy of the offsets, one partial sum per chunk of atoms, and one
+// completion counter per structure) lives in the file-scope array below, which
+// every GPU that loads the library holds until the process exits.
+//
+// Host code cannot use the array's name as a device address; the address is
+// looked up once per device with cudaGetSymbolAddress (that device current) on
+// the first call there, and kept for the life of the process (calls after a
+// cudaDeviceReset are not supported).  Make the first call on a device before
+// any stream capture.
 //
 // The scratch is shared by every call: two calls that overlap on the GPU race
 // on it.  Calls on one stream (or otherwise ordered) are safe; the counters
@@ -53,12 +57,13 @@ d3_status scratch_address(unsigned char** out) {
     return D3_OK;
 }
 
-// Block (s, c) sums the site energies of chunk c of structure s into a partial;
-// the last block of a structure to finish adds the partials in chunk order.
+// Block (c, s) sums the site energies of chunk c of structure s into a partial
+// (chunks on grid x, which has no 65535 limit; structures, at most 16384, on
+// y); the last block of a structure to finish adds the partials in chunk order.
 __global__ void __launch_bounds__(256) k_energy_sums(const long long* __restrict__ off, int maxch,
                                                      const double* __restrict__ e_atom, double* __restrict__ E,
                                                      double* __restrict__ part, unsigned* __restrict__ done) {
-    const int s = blockIdx.x, ch = blockIdx.y;
+    const int ch = blockIdx.x, s = blockIdx.y;
     const long long b = off[s], n = off[s + 1] - b;
     const int nch = (int)((n + kChunk - 1) / kChunk);
     if (n == 0) {
@@ -118,6 +123,6 @@ extern "C" d3_status d3_structure_energies_noalloc(int32_t B, const int64_t* off
     cudaError_t e = cudaMemcpyAsync(off, offsets, sizeof(long long) * (B + 1), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(done, 0, sizeof(unsigned) * B, s);
     if (e != cudaSuccess) return D3_ERR_CUDA;
-    k_energy_sums<<<dim3((unsigned)B, (unsigned)maxch), 256, 0, s>>>(off, (int)maxch, e_atom, E, part, done);
+    k_energy_sums<<<dim3((unsigned)maxch, (unsigned)B), 256, 0, s>>>(off, (int)maxch, e_atom, E, part, done);
     return cudaGetLastError() == cudaSuccess ? D3_OK : D3_ERR_CUDA;
 }

@@ -71,25 +71,41 @@ __device__ __forceinline__ void store_row(T* dst, const T (&v)[8], int rp) {
 }
 
 // W and dW/dn rows of atom p and its projections v_p^(u)_a = sum_b C6ref[u][t][a][b] W_b
+// (and, for the cluster-list dispersion pass, the same rows next to
+// dv_p^(u)_a = sum_b C6ref[u][t][a][b] dW_b in w.vd)
 template <class T, int R>
 __device__ __forceinline__ void store_weights(const Work& w, const Consts& c, const T* __restrict__ c6, int64_t p, int t,
                                               const T (&L)[R], const T (&Wr)[8], const T (&dWr)[8]) {
     store_row<T>((T*)w.W + p * c.RP, Wr, c.RP);
     store_row<T>((T*)w.dW + p * c.RP, dWr, c.RP);
     T* vp = (T*)w.v + p * c.T * c.RP;
+    T* dvp = (sizeof(T) == 4 && w.vd) ? (T*)w.vd + p * c.T * 2 * c.RP : nullptr;  // [T][2][RP] per atom
     for (int u = 0; u < c.T; ++u) {
         const T* cu = c6 + ((size_t)(u * c.T + t) * R) * R;  // C6ref[u][t][a][b]
-        T vr[8];
+        T vr[8], dvr[8];
 #pragma unroll
         for (int a = 0; a < 8; ++a) {
-            T s = 0;
+            T s = 0, ds = 0;
             if (a < R) {
 #pragma unroll
-                for (int b = 0; b < R; ++b) s += cu[a * R + b] * L[b];
+                for (int b = 0; b < R; ++b) {
+                    s += cu[a * R + b] * L[b];
+                    ds += cu[a * R + b] * dWr[b];
+                }
             }
             vr[a] = s;
+            dvr[a] = ds;
         }
         store_row<T>(vp + u * c.RP, vr, c.RP);
+        if (dvp) {
+            store_row<T>(dvp + 2 * u * c.RP, vr, c.RP);
+            store_row<T>(dvp + (2 * u + 1) * c.RP, dvr, c.RP);
+        }
+    }
+    if (w.acc) {  // clear the atom's fixed-point sums of the cluster-list dispersion pass
+        ulonglong2* a = reinterpret_cast<ulonglong2*>(w.acc + 8 * p);
+        const ulonglong2 z = make_ulonglong2(0ull, 0ull);
+        a[0] = z; a[1] = z; a[2] = z; a[3] = z;
     }
 }
 
@@ -551,7 +567,10 @@ cudaError_t forward_impl(const Work& w, const Consts& c, const Tabs& tb, double*
                                                                   tb.dcr, tb.nref, (const T*)tb.c6);
     mark(1);  // the weights (Eq. 3) are formed inside the CN pass
     mark(2);
-    if (w.Nr > 0) {
+    if (MIXED && w.cl_mode && !w_atom) {
+        const cudaError_t e = launch_disp_cl(w, c, tb.pair, e_atom != nullptr, st);
+        if (e != cudaSuccess) return e;
+    } else if (w.Nr > 0) {
         const int TB = w.blk_disp;
         if (w_atom)
             k_disp<MIXED, R, true><<<nblk(w.Nr, TB), TB, c.T * c.T * sizeof(T4), st>>>(w, c, (const T4*)tb.pair);

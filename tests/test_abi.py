@@ -53,3 +53,22 @@ def test_no_gpu_no_fallback(libpath):
     from paper_2310_05279_gb300 import D3, workloads
     with pytest.raises(RuntimeError):
         D3(workloads.carbon_table())
+
+
+def test_noalloc_capacity_checks_launch_nothing(libpath):
+    """The no-allocation entry point rejects sizes beyond its fixed scratch on the host,
+    before any CUDA call (so this runs without a GPU; the pointers are never dereferenced)."""
+    import numpy as np
+    from paper_2310_05279_gb300 import _lib
+    lib = _lib.load()
+    fake = 256  # stands in for device pointers: nothing is enqueued on these paths
+    # one structure of 65537 chunks of 4096 atoms: more partial sums than the scratch holds
+    offs = np.array([0, 65537 * 4096], dtype=np.int64)
+    assert lib.d3_structure_energies_noalloc(1, offs.ctypes.data_as(_lib._lp), fake, fake, None) == _lib.D3_ERR_CAPACITY
+    # more structures than the scratch holds
+    offs = np.zeros(16386, dtype=np.int64)
+    assert lib.d3_structure_energies_noalloc(16385, offs.ctypes.data_as(_lib._lp), fake, fake, None) == \
+        _lib.D3_ERR_CAPACITY
+    # malformed offsets
+    offs = np.array([0, 5, 3], dtype=np.int64)
+    assert lib.d3_structure_energies_noalloc(2, offs.ctypes.data_as(_lib._lp), fake, fake, None) == _lib.D3_ERR_ARG

@@ -37,10 +37,23 @@ sys.path.insert(0, ROOT)
 METRIC = "D3(BJ) E+F+virial atom-steps/s, 1 GB300, mixed vs FP64 form; % of roofline"
 UNIT = "atom-steps/s"
 L2_BYTES = 129 * 1024 * 1024
-# FP32 work the method needs per unique dispersion pair (half-list count, FMA = 2 FLOP):
-# distance 3 + r^2 5 + powers 3 + denominators 2 + reciprocals 2 + C6 and its two CN
-# derivatives 6*Nref + damping sum 3 + energy 2 + dE/dn (both atoms) 4 + force scalar 8
-# + force vector and both atoms' sums 9 + symmetric virial 12 = 53 + 6*Nref.
+# FP32 lane instructions per unique dispersion pair within R_pot, as the
+# measurement contract counts them (FFMA = FMUL = FADD = 1; the C6 bilinear form
+# evaluated directly): 45 + 2 Na Nb + 3 Nb with Na, Nb the numbers of reference
+# CNs of the two elements (Eq. 3).  Over a mix of elements the pair average is
+# 45 + 2 E[Na] E[Nb] + 3 E[Nb], E[N] the atom-fraction weighted reference count.
+def contract_ops_per_pair(tables, types) -> float:
+    nref = np.asarray(tables.nref, dtype=np.float64)
+    frac = np.bincount(np.asarray(types), minlength=len(nref)) / max(1, len(types))
+    en = float((frac * nref).sum())
+    return 45.0 + 2.0 * en * en + 3.0 * en
+
+
+# The factorised FP32 count the kernels implement (FMA = 2 FLOP), kept as a second
+# figure: distance 3 + r^2 5 + powers 3 + denominators 2 + reciprocals 2 + C6 and its
+# two CN derivatives 6*Nref (projections of Eq. 3 per atom) + damping sum 3 + energy 2
+# + dE/dn (both atoms) 4 + force scalar 8 + force vector and both atoms' sums 9 +
+# symmetric virial 12 = 53 + 6*Nref.
 def disp_flops_per_pair(nref: int) -> int:
     return 53 + 6 * nref
 
@@ -90,16 +103,20 @@ def job_value(atoms_per_rank: int, world: int, seconds: float) -> float:
 PAIR_HELPERS = "paper_2310_05279_gb300/csrc/d3gb_pair.cuh"  # device helpers inlined into the pair kernels
 
 
-def kernel_source_sha(path: str, kernel: str):
+def kernel_source_sha(path: str, kernel: str, whole_file: bool = False):
     """SHA-256 of a kernel's definition in a CUDA source (from the line that
-    declares the __global__ function to the first closing brace in column 0)
-    together with the shared pair helpers it inlines."""
+    declares the __global__ function to the first closing brace in column 0),
+    or of the whole file when the kernel's code spans it, together with the
+    shared pair helpers it inlines."""
     import hashlib
     import re
     with open(path) as f:
-        lines = f.read().split("\n")
+        text = f.read()
     with open(os.path.join(ROOT, PAIR_HELPERS)) as f:
         helpers = f.read()
+    if whole_file:
+        return hashlib.sha256((text + "\n" + helpers).encode()).hexdigest()
+    lines = text.split("\n")
     pat = re.compile(r"__global__.*\b" + re.escape(kernel) + r"\(")
     for k, line in enumerate(lines):
         if pat.search(line):
@@ -112,7 +129,7 @@ def kernel_source_sha(path: str, kernel: str):
 
 def recorded_counters(kernel: str):
     """The committed ncu record of `kernel` (profiles/traffic.json), or None when
-    the kernel's definition has changed since the counters were taken."""
+    the kernel's code has changed since the counters were taken."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
@@ -121,7 +138,8 @@ def recorded_counters(kernel: str):
     if not rec:
         return None
     src = os.path.join(ROOT, rec["source"])
-    if not os.path.exists(src) or kernel_source_sha(src, kernel) != rec.get("kernel_sha256"):
+    whole = rec.get("hash_of", "").startswith("the whole file")
+    if not os.path.exists(src) or kernel_source_sha(src, kernel, whole) != rec.get("kernel_sha256"):
         return None
     return rec
 
@@ -344,6 +362,10 @@ def cpu_baseline(batch, params, budget_s=15.0):
     t0 = time.perf_counter()
     oracle.compute(*batch.structure(0), batch.tables, params)
     one = time.perf_counter() - t0
+    if batch.nstruct == 1:  # one structure: the timed call above is the sample
+        n0 = len(batch.structure(0)[0])
+        return {"value": n0 / one, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                "sample": f"1 structure ({n0} atom-steps, {one:.1f} s), FP64 C/OpenMP"}
     nsamp = int(max(1, min(batch.nstruct - 1, budget_s / max(one, 1e-3))))
     idx = list(np.linspace(1, batch.nstruct - 1, nsamp).astype(int))
     t0 = time.perf_counter()
@@ -395,6 +417,164 @@ def run_reference(args):
     return 0
 
 
+def profiled_stages(torch, d3, step, steps, flush, stream):
+    """Per-stage times (ms per call) of `steps` calls with CUDA events between the
+    stages on the launching stream (kernels enqueued directly, not replayed);
+    'lists' is the list-builder kernel alone, inside 'build'."""
+    d3.profile_reset()
+    d3.profile(True)
+    time_steps(torch, step, steps, 1, flush=flush, stream=stream)
+    pr = d3.profile_read()
+    lms, lcalls = d3.profile_stage(7)
+    d3.profile(False)
+    d3.sync_status()
+    st = {k: pr["ms"][k] / max(1, pr["calls"][k]) for k in pr["ms"]}
+    st["lists"] = lms / max(1, lcalls)
+    return st
+
+
+def alu_roofline(kernel, work, t_ms, peak, unit, what, extra=None):
+    """Roofline of an arithmetic-bound kernel: `work` operations per launch over its
+    event-timed duration against `peak` operations per second."""
+    ach = work / (t_ms * 1e-3)
+    d = {"bound": "alu", "kernel": kernel, "achieved": ach / 1e12, "peak": peak / 1e12, "unit": unit,
+         "frac": ach / peak, "algorithmic": what}
+    if extra:
+        d.update(extra)
+    return d
+
+
+def list_roofline(stats, t_ms, hbm_gbs, kernel):
+    """The list builder against the measured HBM copy bandwidth: bytes it must move
+    per launch are the lists it writes (4 B per entry, plus a count per row) and one
+    read of every atom's compact position record (16 B, real and image atoms)."""
+    entries = stats["cluster_list_entries"] + stats["cn_list_entries"] + stats["disp_list_entries"]
+    rows = stats["clusters"] + stats["real_atoms"] * (2 if stats["list_mode"] == 0 else 1)
+    nbytes = 4 * entries + 4 * rows + 16 * (stats["real_atoms"] + stats["image_atoms"])
+    ach = nbytes / (t_ms * 1e-3) / 1e9
+    return {"bound": "hbm", "kernel": kernel, "achieved": ach, "peak": hbm_gbs, "unit": "GB/s",
+            "frac": ach / hbm_gbs, "traffic": recorded_traffic(kernel), "bytes_per_launch": nbytes,
+            "list_bytes_written": 4 * entries,
+            "algorithmic": f"{entries:,} list entries x 4 B + {rows:,} row counts x 4 B + "
+                           f"{stats['real_atoms'] + stats['image_atoms']:,} position records x 16 B"}
+
+
+def run_forward_leg(torch, dev, batch, params, precision, steps, warmup, flush, stream, graphs=True):
+    """Time one batched call per step (neighbour build included, L2 flushed between
+    steps) and profile its stages; returns the step time, stages, list statistics,
+    launch shapes and the autotuner's candidate times."""
+    from paper_2310_05279_gb300 import D3
+    pos = torch.tensor(batch.pos, dtype=torch.float64, device=dev)
+    typ = torch.tensor(batch.types, dtype=torch.int32, device=dev)
+    d3 = D3(batch.tables, params, precision=precision)
+    if not graphs:
+        d3.set_graphs(False)
+    out = d3.compute_batch(pos, typ, batch.offsets, batch.cells, batch.pbc)
+    d3.sync_status()
+
+    def step():
+        d3.compute_batch(pos, typ, batch.offsets, batch.cells, batch.pbc, out=out)
+    t = time_steps(torch, step, steps, warmup, flush=flush, stream=stream)
+    d3.sync_status()
+    ms = statistics.mean(t)
+    stages = profiled_stages(torch, d3, step, max(2, min(steps, 5)), flush, stream)
+    stats = d3.list_stats()
+    res = {"ms_per_step": ms, "value": batch.natoms / (ms * 1e-3), "unit": UNIT, "stage_ms": stages,
+           "lists": stats, "launch_shapes": d3.launch_shapes(), "tune_ms": d3.tune_times()}
+    del d3
+    return res
+
+
+def rooflines(fwd, fp64, batch, peaks, rates, sm_count, fmax, pairs):
+    """Dispersion-pass rooflines on the contract count (FP32 and FP64 forms), the
+    factorised count, the MUFU reciprocal, and the list builder."""
+    nref = int(batch.tables.max_ref)
+    ops = contract_ops_per_pair(batch.tables, batch.types)
+    fp32_peak = sm_count * 128 * fmax
+    mufu_peak = sm_count * 16 * fmax
+    t = fwd["stage_ms"]["disp"]
+    r = {"roofline": alu_roofline(
+        "k_disp_cl (dispersion pass, Eq. 2; stage = image rows + pass + fixed-point finish)", ops * pairs, t,
+        fp32_peak, "T FP32 lane-instructions/s",
+        f"{ops:.1f} FP32 lane instructions per unique pair within R_pot (45 + 2 Na Nb + 3 Nb, FFMA = 1) x "
+        f"{pairs:,} pairs",
+        {"traffic": recorded_traffic("k_disp_cl"), "pipes": recorded_pipes("k_disp_cl"),
+         "peak_source": f"{sm_count} SMs x 128 FP32 lanes x {fmax / 1e6:.0f} MHz (sm_max_mhz of MEASURED_PEAKS.json)",
+         "measured_ffma_rate": rates["fp32_lane_ops_per_s"] / 1e12,
+         "timing": "dispersion stage events over the profiled steps (kernels enqueued directly)"})}
+    fl = disp_flops_per_pair(nref)
+    r["roofline_factorised"] = alu_roofline(
+        "k_disp_cl", fl * pairs, t, 2 * fp32_peak, "TFLOP/s",
+        f"{fl} FLOP (FMA = 2) per unique pair, the per-atom C6 projections of Eq. 3 counted once per pair")
+    r["mufu"] = alu_roofline(
+        "k_disp_cl", 1.0 * pairs, t, mufu_peak, "T MUFU ops/s",
+        "one reciprocal (rcp) per unique pair: 1/((r^6 + R^6)(r^8 + R^8))",
+        {"measured_mufu_rate": rates["mufu_ops_per_s"] / 1e12})
+    r["build_roofline"] = list_roofline(fwd["lists"], fwd["stage_ms"]["lists"], float(peaks["hbm_gbs"]),
+                                        "k_build_clist")
+    if fp64 is not None:
+        r["fp64_roofline"] = alu_roofline(
+            "k_disp<FP64> (per-atom full lists: each pair evaluated from both atoms)", ops * pairs,
+            fp64["stage_ms"]["disp"], rates["fp64_lane_ops_per_s"], "T FP64 lane-instructions/s",
+            f"{ops:.1f} lane instructions per unique pair (DFMA = 1) x {pairs:,} pairs",
+            {"peak_source": "measured DFMA lane rate (d3_peak_rates: independent FMA chains, 8 blocks of 256 "
+                            "threads per SM, best of 3)"})
+    return r
+
+
+def box_leg(torch, dev, params, steps, flush, stream, peaks, rates, sm_count, fmax, md_steps, md_skin):
+    """The 1,048,576-atom box as one call (build included), mixed and FP64, with its
+    rooflines; the NVE loop with list reuse; the oracle on a 2,048-atom periodic box
+    of the same generator as the CPU baseline."""
+    from paper_2310_05279_gb300 import workloads as wl
+    b = wl.mof_like_box()
+    mixed = run_forward_leg(torch, dev, b, params, "mixed", steps, 2, flush, stream)
+    fp64 = run_forward_leg(torch, dev, b, params, "fp64", 2, 1, flush, stream)
+    pairs = int(mixed["lists"]["pairs_within_rpot"])
+    res = {"workload": f"mof_like_box: {b.natoms:,} atoms (H:C:N:O:Zn = 40:36:8:12:4), 262.45 A cube, one call "
+                       "per step with the neighbour build", "mixed": mixed,
+           "fp64": {k: fp64[k] for k in ("ms_per_step", "value", "unit", "stage_ms")},
+           "mixed_speedup": fp64["ms_per_step"] / mixed["ms_per_step"], "pairs_within_rpot": pairs}
+    res.update(rooflines(mixed, fp64, b, peaks, rates, sm_count, fmax, pairs))
+    if md_steps > 0:
+        res["md_loop"] = md_leg(torch, dev, params, md_steps, skin=md_skin)
+    small = wl.mof_like_box(ncell=8)
+    res["cpu_baseline"] = cpu_baseline(small, params, budget_s=8.0)
+    res["cpu_baseline"]["sample"] += " (2,048-atom periodic box of the same generator: same density and mix)"
+    return res
+
+
+def uneven_leg(torch, dev, params, steps, flush, stream):
+    """The 512-structure uneven batch (config 3) in one call, mixed and FP64, and by
+    size class (each class its own batched call and handle), with the launch shapes
+    the autotuner chose and the times it measured for the candidates."""
+    from paper_2310_05279_gb300 import workloads as wl
+    b = wl.uneven_batch()
+    sizes = np.diff(b.offsets)
+    res = {"workload": f"uneven_batch: {b.nstruct} triclinic structures of 50-4000 atoms ({b.natoms:,} atoms)"}
+    res["whole"] = run_forward_leg(torch, dev, b, params, "mixed", steps, 2, flush, stream)
+    f64 = run_forward_leg(torch, dev, b, params, "fp64", 2, 1, flush, stream)
+    res["whole_fp64"] = {k: f64[k] for k in ("ms_per_step", "value", "unit", "stage_ms")}
+    res["mixed_speedup"] = f64["ms_per_step"] / res["whole"]["ms_per_step"]
+    classes = []
+    for lo, hi in ((50, 200), (200, 1000), (1000, 4001)):
+        idx = [int(s) for s in np.nonzero((sizes >= lo) & (sizes < hi))[0]]
+        if not idx:
+            continue
+        sub = b.subset(idx)
+        m = run_forward_leg(torch, dev, sub, params, "mixed", steps, 2, flush, stream)
+        f = run_forward_leg(torch, dev, sub, params, "fp64", 2, 1, flush, stream)
+        tm = m["tune_ms"]
+        spread = {k: (max(v) / min(v) - 1.0) if min(v) > 0 else None for k, v in tm.items()}
+        classes.append({"sizes": f"{lo}-{hi - 1}", "structures": len(idx), "atoms": sub.natoms,
+                        "mixed": m["value"], "mixed_ms": m["ms_per_step"], "fp64": f["value"],
+                        "fp64_ms": f["ms_per_step"], "mixed_speedup": f["ms_per_step"] / m["ms_per_step"],
+                        "unit": UNIT, "launch_shapes": m["launch_shapes"], "autotune_candidate_ms": tm,
+                        "autotune_spread": spread})
+    res["size_classes"] = classes
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -412,6 +592,9 @@ def main():
     ap.add_argument("--backward-steps", type=int, default=5, help="steps of the backward leg (0: skip)")
     ap.add_argument("--three-body-steps", type=int, default=5,
                     help="steps of the extra leg with the optional three-body term (0: skip)")
+    ap.add_argument("--box-steps", type=int, default=5,
+                    help="steps of the 1M-atom box leg, one call each (0: skip the box leg)")
+    ap.add_argument("--uneven-steps", type=int, default=5, help="steps of the uneven-batch leg (0: skip)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -426,7 +609,7 @@ def main():
     dev = torch.device("cuda", local if world > 1 else 0)
     torch.cuda.set_device(dev)
 
-    from paper_2310_05279_gb300 import D3, workloads as wl
+    from paper_2310_05279_gb300 import D3, peak_rates, workloads as wl
     from paper_2310_05279_gb300 import build as libbuild
     libbuild.build()
     batch = rank_batch(rank)
@@ -467,38 +650,37 @@ def main():
     clocks = clk.stop()
     launches_per_step = d3.profile_read()["launches"] / max(1, args.steps)
     shapes = d3.launch_shapes()
+    tune_ms = d3.tune_times()
     d3.sync_status()
     ms = reduce_max(sum(times) / len(times), dev)
     value = job_value(N, world, ms * 1e-3)
 
-    # stage breakdown and the dominant kernel, the dispersion pass (Eq. 2): the same
-    # steps again with CUDA events between the stages on the launching stream (the
-    # kernels are then enqueued directly instead of replayed as a graph)
-    d3.profile_reset()
-    d3.profile(True)
-    time_steps(torch, step, args.steps, 1, flush=flush, stream=stream)
-    prof = d3.profile_read()
-    d3.profile(False)
-    d3.sync_status()
-    stage_ms = {k: prof["ms"][k] / max(1, prof["calls"][k]) for k in prof["ms"]}
-    dom = max(stage_ms, key=lambda k: stage_ms[k])
+    # stage breakdown of the same steps with CUDA events between the stages on the
+    # launching stream (the kernels are then enqueued directly instead of replayed)
+    stage_ms = profiled_stages(torch, d3, step, args.steps, flush, stream)
+    stats = d3.list_stats()
+    dom = max((k for k in stage_ms if k != "lists"), key=lambda k: stage_ms[k])
+    fwd = {"stage_ms": stage_ms, "lists": stats}
 
     # FP64 form on the same batch
     fp64 = None
     if args.fp64_steps > 0:
-        d3f = D3(batch.tables, params, precision="fp64")
-        outf = d3f.compute_batch(pos, typ, batch.offsets, batch.cells, batch.pbc)
-        d3f.sync_status()
-        d3f.profile(True)
-        tf = time_steps(torch, lambda: d3f.compute_batch(pos, typ, batch.offsets, batch.cells, batch.pbc, out=outf),
-                        args.fp64_steps, 1, flush=flush, stream=stream)
-        proff = d3f.profile_read()
-        d3f.profile(False)
-        msf = reduce_max(sum(tf) / len(tf), dev)
-        del d3f
+        f = run_forward_leg(torch, dev, batch, params, "fp64", args.fp64_steps, 1, flush, stream)
+        msf = reduce_max(f["ms_per_step"], dev)
         fp64 = {"value": job_value(N, world, msf * 1e-3), "unit": UNIT, "ms_per_step": msf, "dtype": "f64",
-                "stage_ms": {k: proff["ms"][k] / max(1, proff["calls"][k]) for k in proff["ms"]},
-                "mixed_speedup": msf / ms}
+                "stage_ms": f["stage_ms"], "mixed_speedup": msf / ms, "lists": f["lists"]}
+
+    # measured arithmetic rates and the rooflines of the dispersion pass and the list build
+    peaks, peak_kind = measured_peaks()
+    rates = peak_rates()
+    props = torch.cuda.get_device_properties(dev)
+    sm_count = props.multi_processor_count
+    fmax = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    pairs = int(stats["pairs_within_rpot"])
+    pairs_host = count_pairs(torch, batch, params["rc_disp"], dev)
+    roofs = rooflines(fwd, fp64, batch, peaks, rates, sm_count, fmax, pairs)
+    roofs["roofline"]["pairs_check"] = {"counted_by_pass": pairs, "counted_on_host": pairs_host}
+    roofs["roofline"]["peak_kind"] = peak_kind
 
     # the optional three-body term (not part of the paper's model) on the same batch:
     # the whole step with it on, and its own pass against the FP32 roofline
@@ -512,25 +694,37 @@ def main():
         def step_atm():
             d3a.compute_batch(pos, typ, batch.offsets, batch.cells, batch.pbc, out=outa)
         ta = time_steps(torch, step_atm, args.three_body_steps, 3, flush=flush, stream=stream)
-        d3a.profile(True)
-        time_steps(torch, step_atm, args.three_body_steps, 1, flush=flush, stream=stream)
-        profa = d3a.profile_read()
-        d3a.profile(False)
-        d3a.sync_status()
+        stage_a = profiled_stages(torch, d3a, step_atm, args.three_body_steps, flush, stream)
         del d3a
         msa = reduce_max(sum(ta) / len(ta), dev)
-        stage_a = {k: profa["ms"][k] / max(1, profa["calls"][k]) for k in profa["ms"]}
         tri = count_triangles(torch, batch, atm["rc3"], dev)
+        nref = int(batch.tables.max_ref)
+        fl = atm_flops_per_triangle(nref)
+        tf = fl * tri / (stage_a["three_body"] * 1e-3) / 1e12
+        fp32_flops = sm_count * 128 * 2 * fmax / 1e12
         three_body = {"value": job_value(N, world, msa * 1e-3), "unit": UNIT, "ms_per_step": msa,
                       "three_body_ms": stage_a["three_body"], "stage_ms": stage_a, "triangles": tri,
                       "params": atm, "note": "optional triple-dipole term; the paper's model leaves it out",
-                      "flop_per_triangle": None}
+                      "flop_per_triangle": fl,
+                      "roofline": {"bound": "alu", "kernel": "k_atm", "achieved": tf, "peak": fp32_flops,
+                                   "unit": "TFLOP/s", "frac": tf / fp32_flops, "traffic": recorded_traffic("k_atm"),
+                                   "pipes": recorded_pipes("k_atm"),
+                                   "algorithmic": f"{fl} FLOP per unique triangle x {tri:.4g}"}}
 
     # the hand-written backward on the damping-refit batch
     backward = backward_leg(torch, dev, params, args.backward_steps) if args.backward_steps > 0 else None
 
-    # the 1M-atom box as an MD loop, with the lists reused between rebuilds
-    md = md_leg(torch, dev, params, args.md_steps, skin=args.md_skin) if args.md_steps > 0 else None
+    # the 1M-atom box (one call per step, and the NVE loop with list reuse)
+    box = None
+    if args.box_steps > 0 and rank == 0:
+        box = box_leg(torch, dev, params, args.box_steps, flush, stream, peaks, rates, sm_count, fmax,
+                      args.md_steps, args.md_skin)
+    md = box.get("md_loop") if box else (md_leg(torch, dev, params, args.md_steps, skin=args.md_skin)
+                                         if args.md_steps > 0 else None)
+
+    # the uneven batch, whole and by size class
+    uneven = uneven_leg(torch, dev, params, args.uneven_steps, flush, stream) \
+        if args.uneven_steps > 0 and rank == 0 else None
 
     # end to end through the host-memory entry point (pinned buffers, copies inside)
     e2e = None
@@ -555,50 +749,30 @@ def main():
                "d2h_bytes_per_step": batch.nstruct * 8 + N * 3 * 8 + batch.nstruct * 9 * 8,
                "entry_point": "d3_compute_batch_host (pinned host buffers)"}
 
-    # roofline of the dispersion pass: FP32 pipe, FMA = 2 FLOP
-    peaks, peak_kind = measured_peaks()
-    props = torch.cuda.get_device_properties(dev)
-    sm_count = props.multi_processor_count
-    fmax = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
-    fp32_peak = sm_count * 128 * 2 * fmax / 1e12  # TFLOP/s
-    pairs = count_pairs(torch, batch, params["rc_disp"], dev)
-    nref = int(batch.tables.max_ref)
-    disp_tflops = disp_flops_per_pair(nref) * pairs / (stage_ms["disp"] * 1e-3) / 1e12
-    roof = {"bound": "alu", "kernel": "k_disp (dispersion pass, Eq. 2)", "achieved": disp_tflops,
-            "peak": fp32_peak, "unit": "TFLOP/s", "frac": disp_tflops / fp32_peak,
-            "traffic": recorded_traffic("k_disp"), "pipes": recorded_pipes("k_disp"),
-            "peak_source": f"{sm_count} SMs x 128 FP32 lanes x 2 x {fmax/1e6:.0f} MHz (sm_max_mhz, {peak_kind})",
-            "algorithmic": f"{disp_flops_per_pair(nref)} FLOP per unique pair within 12 A x {pairs:.4g} pairs",
-            "timing": "k_disp stage events over the same number of steps, kernels enqueued directly"}
-
-    if three_body is not None:
-        fl = atm_flops_per_triangle(nref)
-        tf = fl * three_body["triangles"] / (three_body["three_body_ms"] * 1e-3) / 1e12
-        three_body["flop_per_triangle"] = fl
-        three_body["roofline"] = {"bound": "alu", "kernel": "k_atm", "achieved": tf, "peak": fp32_peak,
-                                  "unit": "TFLOP/s", "frac": tf / fp32_peak, "traffic": recorded_traffic("k_atm"),
-                                  "pipes": recorded_pipes("k_atm"),
-                                  "algorithmic": f"{fl} FLOP per unique triangle x {three_body['triangles']:.4g}"}
-
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "bilayer_scan: 128 AB-graphene bilayers x 1440 C atoms (184,320 atoms), "
                                    "d 2.8-8.0 A x 8 slides", "structures": batch.nstruct, "atoms": N,
-                       "precision": "mixed (FP32 pair math, FP64 accumulation)", "rc_disp_A": 12.0, "rc_cn_A": 6.0,
-                       "neighbour_build": "every step", "l2": "flushed between timed steps",
+                       "precision": "mixed (FP32 pair math; fixed-point, compensated and FP64 sums)",
+                       "rc_disp_A": 12.0, "rc_cn_A": 6.0, "neighbour_build": "every step",
+                       "l2": "flushed between timed steps",
                        "launch": "direct" if args.no_graphs else "graph replay of the steady-state call",
-                       "launch_shapes": {**shapes, "how": "measured by the library's autotuner at plan time"},
+                       "launch_shapes": {**shapes, "how": "measured by the library's autotuner at plan time",
+                                         "candidate_ms": tune_ms},
                        "parallelism": f"data-parallel x{world}: each rank its own 128-structure scan "
                                       "(jitter seed 1 + rank), no collective on the data path"},
-            "roofline": roof,
-            "stage_ms": stage_ms, "dominant_stage": dom,
+            **roofs,
+            "rates": {k: v / 1e12 for k, v in rates.items()}, "rates_unit": "T ops/s (measured on this GPU)",
+            "stage_ms": stage_ms, "dominant_stage": dom, "lists": stats,
             "split": {"with_build": value,
                       "without_build": job_value(N, world, max(1e-9, ms - stage_ms["build"]) * 1e-3),
                       "unit": UNIT,
                       "how": "the timed step minus the neighbour-build stage of the profiled pass (the build "
                              "runs in every timed step; with a skin it is amortised over the steps between rebuilds)"},
             "fp64_form": fp64,
+            "mof_like_box": box,
+            "uneven_batch": uneven,
             "three_body": three_body,
             "md_loop": md,
             "backward": backward,

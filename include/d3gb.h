@@ -283,6 +283,33 @@ d3_status d3_profile_read(d3_handle *h, double *ms, int64_t *calls, int64_t *lau
 /* Zero the stage totals and the launch counter. */
 d3_status d3_profile_reset(d3_handle *h);
 
+/* Totals of one profiled stage since the last reset: stage 0..6 as in
+ * d3_profile_read, stage 7 the list-builder kernel alone (inside stage 0).
+ * ms and calls may be NULL.  D3_ERR_ARG for another stage number. */
+d3_status d3_profile_stage(d3_handle *h, int32_t stage, double *ms, int64_t *calls);
+
+/* Sizes of the current plan's neighbour data, for measurement (synchronises):
+ * stats[0] real atoms, [1] image atoms, [2] clusters of the cluster lists,
+ * [3] cluster-list entries (last build in cluster mode, else 0), [4] CN-list
+ * entries, [5] per-atom dispersion-list entries (last build with full lists,
+ * else 0), [6] unique pair instances within R_pot evaluated by the last
+ * cluster-mode dispersion pass (Eq. 2), [7] list mode of the last build
+ * (1 = cluster lists, 0 = full per-atom lists, -1 = none).  host int64_t[8]. */
+d3_status d3_list_stats(d3_handle *h, int64_t *stats);
+
+/* The autotuner's last measurement, host float[8] in ms: list build, CN pass,
+ * dispersion pass and chain pass, each with the 64- and 128-thread (or 8 and
+ * 16 blocks per SM) candidate.  Zeros before the first measurement. */
+d3_status d3_tune_times(d3_handle *h, float *ms);
+
+/* Measured arithmetic rates of the current device, the denominators of the
+ * rooflines of the pair passes: rates[0] FP32 FMA lane operations per second,
+ * rates[1] FP64 FMA lane operations per second, rates[2] MUFU reciprocals per
+ * second (host double[3]).  Runs three short microbenchmark kernels on
+ * `stream` and synchronises; allocates a small scratch buffer.  A measurement
+ * helper: the paper has no counterpart. */
+d3_status d3_peak_rates(double *rates, void *stream);
+
 /* Per-structure energies from site energies, for callers that cannot allocate
  * device memory: a host program that keeps all device memory in its own pool
  * and hands libraries only the buffers it owns, or a loop that cannot take the

@@ -252,6 +252,29 @@ class D3:
         """Add E, F, W into the output tensors instead of overwriting them (Eq. 9 coupling)."""
         self._check(self.lib.d3_set_accumulate(self.h, 1 if on else 0))
 
+    def profile_stage(self, stage: int):
+        """(ms, calls) of one profiled stage; stage 7 is the list-builder kernel alone."""
+        ms = C.c_double()
+        calls = C.c_int64()
+        self._check(self.lib.d3_profile_stage(self.h, int(stage), C.byref(ms), C.byref(calls)))
+        return ms.value, calls.value
+
+    STAT_KEYS = ("real_atoms", "image_atoms", "clusters", "cluster_list_entries", "cn_list_entries",
+                 "disp_list_entries", "pairs_within_rpot", "list_mode")
+
+    def list_stats(self) -> dict:
+        """Sizes of the neighbour data of the current plan (d3_list_stats; synchronises)."""
+        st = (C.c_int64 * 8)()
+        self._check(self.lib.d3_list_stats(self.h, st))
+        return dict(zip(self.STAT_KEYS, list(st)))
+
+    def tune_times(self) -> dict:
+        """The autotuner's last measurement (ms per stage and candidate)."""
+        t = (C.c_float * 8)()
+        self._check(self.lib.d3_tune_times(self.h, t))
+        v = list(t)
+        return {"build": v[0:2], "cn": v[2:4], "disp": v[4:6], "chain": v[6:8]}
+
     def build_count(self) -> int:
         """Neighbour builds executed on the device so far (synchronises)."""
         n = C.c_int64()
@@ -273,6 +296,16 @@ def heat_current(w_atom, vel, stream=None):
     return J
 
 
+def peak_rates(stream=None) -> dict:
+    """Measured FP32 FMA, FP64 FMA and MUFU reciprocal rates of the current device (d3_peak_rates)."""
+    lib = _lib.load()
+    r = (C.c_double * 3)()
+    st = lib.d3_peak_rates(r, _stream_ptr(stream))
+    if st != _lib.D3_OK:
+        raise D3Error(st, "d3_peak_rates failed")
+    return {"fp32_lane_ops_per_s": r[0], "fp64_lane_ops_per_s": r[1], "mufu_ops_per_s": r[2]}
+
+
 def version() -> str:
     return _lib.load().d3_version().decode()
 
@@ -285,7 +318,9 @@ def _autograd_function():
 
         apply(pos, theta, d3, types, offsets, cells, pbc): pos cuda float64 (N,3) [A],
         theta cuda float64 (4,) = (s6, s8, a1, a2[bohr]).  Returns E (B,) [eV] and F (N,3)
-        [eV/A].  Gradients flow to pos and theta (the backward runs in FP64)."""
+        [eV/A].  Gradients flow to pos and theta; the backward runs in the handle's
+        precision (FP64 duals for an FP64 handle; for a mixed handle the forward's mixed
+        arithmetic with FP32 tangents)."""
 
         @staticmethod
         def forward(ctx, pos, theta, d3, types, offsets, cells, pbc):

@@ -57,6 +57,10 @@ SIGNATURES = {
     "d3_profile_read": (C.c_int, [_vp, _dp, _lp, _lp]),
     "d3_profile_reset": (C.c_int, [_vp]),
     "d3_structure_energies_noalloc": (C.c_int, [C.c_int32, _lp, _vp, _vp, _vp]),
+    "d3_profile_stage": (C.c_int, [_vp, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
+    "d3_list_stats": (C.c_int, [_vp, C.POINTER(C.c_int64)]),
+    "d3_tune_times": (C.c_int, [_vp, C.POINTER(C.c_float)]),
+    "d3_peak_rates": (C.c_int, [C.POINTER(C.c_double), _vp]),
 }
 
 _lib = None

@@ -21,7 +21,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", "-I" + INCLUDE]
 SOURCES = ["d3gb_build.cu", "d3gb_passes.cu", "d3gb_cluster.cu", "d3gb_atm.cu", "d3gb_backward.cu", "d3gb_api.cu",
-           "d3gb_noalloc.cu"]
+           "d3gb_noalloc.cu", "d3gb_peaks.cu"]
 
 
 def _nvcc() -> str:

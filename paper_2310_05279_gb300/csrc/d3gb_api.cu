@@ -23,7 +23,7 @@
 
 namespace d3gb {
 cudaError_t launch_build_impl(const Work& w, const double* pos, const int32_t* types, const double* rk_tab,
-                              int* bsum, cudaStream_t st);
+                              int* bsum, cudaStream_t st, cudaEvent_t* lmarks = nullptr);
 int64_t scan_scratch_ints(int64_t ncells);
 cudaError_t launch_backward(const Work& w, const Consts& c, const double* c6d, const dbl4* paird,
                             const double* cnref, const int* nref, const Tabs& tbm, const double* dLdE,
@@ -38,7 +38,10 @@ namespace {
 
 constexpr int kWindowCells = 3;  // list radius spans at most this many cells per axis
 // profiled stages: build, CN (with the Eq. 3 weights), weights, dispersion, three-body, chain, finalize
+// (d3_profile_read), and the list-builder kernel inside the build (d3_profile_stage)
 constexpr int kStages = 7;
+constexpr int kStagesAll = 8;
+constexpr int kEvents = kStages + 3;  // kStages + 1 stage boundaries, 2 around the list builder
 
 // Launch shapes: threads per block of the CN, dispersion and chain passes, and
 // list-builder blocks per SM.  The defaults are the fastest shapes on the
@@ -91,6 +94,7 @@ struct Plan {
     double* bwd_scratch = nullptr;
     int64_t bwd_scratch_n = 0;
     unsigned long long* acc = nullptr;  // fixed-point sums of the cluster-list dispersion pass
+    unsigned long long* npairs = nullptr;  // pair count of the cluster-list dispersion pass
     float* vd = nullptr;                // C6 projections (v, dv) per atom of the cluster-list dispersion pass
 };
 
@@ -98,6 +102,7 @@ struct Plan {
 void set_mode(Plan& P, int mode) {
     P.w.cl_mode = mode == kClusterLists ? 1 : 0;
     P.w.acc = mode == kClusterLists ? P.acc : nullptr;
+    P.w.npairs = mode == kClusterLists ? P.npairs : nullptr;
     P.w.vd = mode == kClusterLists ? P.vd : nullptr;
 }
 
@@ -139,8 +144,9 @@ struct d3_handle {
     bool prof_on = false;
     std::vector<cudaEvent_t> ev_pool;
     std::vector<std::vector<cudaEvent_t>> ev_pending;
-    double prof_ms[kStages] = {};
-    int64_t prof_calls[kStages] = {};
+    double prof_ms[kStagesAll] = {};
+    int64_t prof_calls[kStagesAll] = {};
+    float tune_ms[8] = {};  // last autotuner measurement: build, CN, dispersion, chain x 2 candidates
     int64_t launches = 0;
     bool accumulate = false;  // d3_set_accumulate
     // replay of the steady-state call as one CUDA graph (captured on cap_stream)
@@ -446,6 +452,9 @@ d3_status plan_alloc(d3_handle* h, Plan& P) {
     A(w.nbr_cl, int, lcl);
     A(w.cnt_cl, int, std::max<int64_t>(1, ncl));
     A(w.acc, unsigned long long, 8 * Nr);
+    A(w.npairs, unsigned long long, 1);
+    // rows of v and dv for real and image atoms (whether images get copies of their
+    // source's rows is decided after the sizing pass, from the image count)
     if (h->prm.precision == D3_MIXED) A(w.vd, float, Nt * h->T * 2 * h->RP);
     A(w.gate, int, 1);
     A(w.xref, double, 3 * Nr);
@@ -489,6 +498,8 @@ d3_status plan_alloc(d3_handle* h, Plan& P) {
     P.w.clu_sid = dclu;
     P.w.ncl = ncl;
     P.acc = w.acc;  // attached to the Work of cluster-mode calls only
+    P.npairs = w.npairs;
+    P.w.npairs = nullptr;
     P.vd = w.vd;
     P.w.acc = nullptr;
     P.w.vd = nullptr;
@@ -582,7 +593,7 @@ std::array<int, 4> size_class(const d3_handle* h, const Plan& P) {
 // check first decides on the device whether the build runs; the sorted
 // positions are rewritten either way.
 d3_status enqueue_build(d3_handle* h, Plan& P, const double* pos, const int32_t* types, cudaStream_t st, int mode,
-                        bool gated = false) {
+                        bool gated = false, cudaEvent_t* lmarks = nullptr) {
     // a build in the other list mode re-sorted the atoms: the first build in
     // this mode must run whatever the displacement check would decide
     if (P.last_mode != mode) gated = false;
@@ -597,9 +608,9 @@ d3_status enqueue_build(d3_handle* h, Plan& P, const double* pos, const int32_t*
         if (e != cudaSuccess) return cuda_fail(h, e, "displacement check");
         if (P.Nr > 0) h->launches += 1;
     }
-    e = launch_build_impl(w, pos, types, h->d_rk, P.bsum, st);
+    e = launch_build_impl(w, pos, types, h->d_rk, P.bsum, st, lmarks);
     if (e != cudaSuccess) return cuda_fail(h, e, "neighbour build launch");
-    if (P.Nr > 0) h->launches += kBuildLaunches + (mode == kClusterLists && P.ncl > 0 ? 1 : 0);
+    if (P.Nr > 0) h->launches += kBuildLaunches;
     return D3_OK;
 }
 
@@ -658,7 +669,7 @@ d3_status tune_shapes(d3_handle* h, Plan& P, const double* pos, const int32_t* t
             if (e == cudaSuccess) e = launch_forward(w, c, mixed, tb, E, F, W, nullptr, nullptr, nullptr, P.B, st,
                                                      ev.data() + 1);
             if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-            h->launches += kBuildLaunches + kForwardLaunches + c.atm + 2 * w.cl_mode;
+            h->launches += kBuildLaunches + kForwardLaunches + c.atm + w.cl_mode * (1 + w.vd_images);
             const int from[4] = {0, 1, 3, 5};
             for (int m = 0; m < 4 && e == cudaSuccess; ++m) {
                 float ms = 0.f;
@@ -677,6 +688,8 @@ d3_status tune_shapes(d3_handle* h, Plan& P, const double* pos, const int32_t* t
                          kDefaultShape[1] == kBlockCand[0] ? 0 : 1, kDefaultShape[2] == kBlockCand[0] ? 0 : 1};
     int pick[4];
     for (int m = 0; m < 4; ++m) pick[m] = t[m][1 - dflt[m]] < 0.99f * t[m][dflt[m]] ? 1 - dflt[m] : dflt[m];
+    for (int m = 0; m < 4; ++m)
+        for (int k = 0; k < 2; ++k) h->tune_ms[2 * m + k] = t[m][k];
     const std::array<int32_t, 4> chosen = {kBlockCand[pick[1]], kBlockCand[pick[2]], kBlockCand[pick[3]],
                                            kBuildCand[pick[0]]};
     h->shape_cache[key] = chosen;
@@ -737,6 +750,9 @@ d3_status ensure_plan(d3_handle* h, int32_t B, const int64_t* offsets, const dou
             if (mx[3 * s2 + 2] > G.cap_cl) { G.cap_cl = round_cap(mx[3 * s2 + 2] * 1.1 + 16); grow = true; }
         }
         if (!grow) {
+            // image rows of v and dv are copies of their source's when that is cheap
+            // (few images, or few types); otherwise the pass resolves each image's source
+            P.w.vd_images = (int64_t)gcount * h->T <= 2 * P.Nr ? 1 : 0;
             P.sized[mode] = true;
             return tune_shapes(h, P, pos, types, st, mode);
         }
@@ -783,19 +799,20 @@ d3_status forward(d3_handle* h, int32_t B, const int64_t* offsets, const double*
     Plan& P = h->plan;
     std::vector<cudaEvent_t> ev;
     if (h->prof_on) {
-        ev = take_events(h, kStages + 1);
-        if (ev.size() == kStages + 1) cudaEventRecord(ev[0], st);
+        ev = take_events(h, kEvents);
+        if (ev.size() == kEvents) cudaEventRecord(ev[0], st);
     }
-    s = enqueue_build(h, P, pos, types, st, mode, h->prm.skin_A > 0);
+    s = enqueue_build(h, P, pos, types, st, mode, h->prm.skin_A > 0,
+                      ev.size() == kEvents ? ev.data() + kStages + 1 : nullptr);
     if (s != D3_OK) return s;
     const Consts c = make_consts(h);
     const bool mixed = h->prm.precision == D3_MIXED;
     const Tabs tb = forward_tabs(h);
     cudaError_t e = launch_forward(P.w, c, mixed, tb, E, F, W, e_atom, cn, w_atom, B, st,
-                                   ev.size() == kStages + 1 ? ev.data() + 1 : nullptr);
+                                   ev.size() == kEvents ? ev.data() + 1 : nullptr);
     if (e != cudaSuccess) return cuda_fail(h, e, "forward launch");
-    h->launches += (P.Nr > 0 ? kForwardLaunches + c.atm + (mode == kClusterLists ? 1 : 0) : 1);
-    if (ev.size() == kStages + 1) h->ev_pending.push_back(ev);
+    h->launches += (P.Nr > 0 ? kForwardLaunches + c.atm + (mode == kClusterLists ? 1 + P.w.vd_images : 0) : 1);
+    if (ev.size() == kEvents) h->ev_pending.push_back(ev);
     else for (cudaEvent_t x : ev) h->ev_pool.push_back(x);
     return D3_OK;
 }
@@ -1258,6 +1275,12 @@ d3_status d3_profile_read(d3_handle* h, double* ms, int64_t* calls, int64_t* lau
                 h->prof_calls[k] += 1;
             }
         }
+        float t = 0.f;  // the list builder (recorded when the build ran that kernel)
+        if (cudaEventElapsedTime(&t, v[kStages + 1], v[kStages + 2]) == cudaSuccess) {
+            h->prof_ms[kStages] += t;
+            h->prof_calls[kStages] += 1;
+        }
+        cudaGetLastError();
         for (cudaEvent_t x : v) h->ev_pool.push_back(x);
     }
     h->ev_pending.clear();
@@ -1272,12 +1295,62 @@ d3_status d3_profile_read(d3_handle* h, double* ms, int64_t* calls, int64_t* lau
 d3_status d3_profile_reset(d3_handle* h) {
     if (!h) return D3_ERR_ARG;
     d3_status s = d3_profile_read(h, nullptr, nullptr, nullptr);
-    for (int k = 0; k < kStages; ++k) {
+    for (int k = 0; k < kStagesAll; ++k) {
         h->prof_ms[k] = 0;
         h->prof_calls[k] = 0;
     }
     h->launches = 0;
     return s;
+}
+
+
+d3_status d3_profile_stage(d3_handle* h, int32_t stage, double* ms, int64_t* calls) {
+    if (!h || stage < 0 || stage >= kStagesAll) return D3_ERR_ARG;
+    d3_status s = d3_profile_read(h, nullptr, nullptr, nullptr);
+    if (s != D3_OK) return s;
+    if (ms) *ms = h->prof_ms[stage];
+    if (calls) *calls = h->prof_calls[stage];
+    return D3_OK;
+}
+
+d3_status d3_list_stats(d3_handle* h, int64_t* stats) {
+    if (!h || !stats) return D3_ERR_ARG;
+    for (int k = 0; k < 8; ++k) stats[k] = 0;
+    Plan& P = h->plan;
+    if (!P.valid) return D3_OK;
+    cudaError_t e = cudaStreamSynchronize(h->last_stream);
+    auto sum_ints = [&](const int* d, int64_t n, int64_t* out) {
+        if (e != cudaSuccess || !d || n <= 0) return;
+        std::vector<int> v((size_t)n);
+        e = cudaMemcpy(v.data(), d, sizeof(int) * (size_t)n, cudaMemcpyDeviceToHost);
+        int64_t t = 0;
+        for (int x : v) t += x;
+        *out = t;
+    };
+    stats[0] = P.Nr;
+    int ng = 0;
+    if (e == cudaSuccess && P.ncells > 0)
+        e = cudaMemcpy(&ng, P.w.start_ghost + P.ncells, sizeof(int), cudaMemcpyDeviceToHost);
+    stats[1] = ng;
+    stats[2] = P.ncl;
+    const bool cl = P.last_mode == kClusterLists;
+    if (cl) sum_ints(P.w.cnt_cl, P.ncl, &stats[3]);
+    sum_ints(P.w.cnt_cn, P.Nr, &stats[4]);
+    if (!cl) sum_ints(P.w.cnt_disp, P.Nr, &stats[5]);
+    if (e == cudaSuccess && cl && P.npairs) {
+        unsigned long long np = 0;
+        e = cudaMemcpy(&np, P.npairs, sizeof(np), cudaMemcpyDeviceToHost);
+        stats[6] = (int64_t)np;
+    }
+    stats[7] = P.last_mode;
+    if (e != cudaSuccess) return cuda_fail(h, e, "list statistics");
+    return D3_OK;
+}
+
+d3_status d3_tune_times(d3_handle* h, float* ms) {
+    if (!h || !ms) return D3_ERR_ARG;
+    for (int k = 0; k < 8; ++k) ms[k] = h->tune_ms[k];
+    return D3_OK;
 }
 
 }  // extern "C"

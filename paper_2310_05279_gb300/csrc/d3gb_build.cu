@@ -863,9 +863,10 @@ cudaError_t scan(const int* cnt, int* start, int* bsum, int64_t n, const int* ga
 // The cell-list build: counters, binning, images, sort, fill, lists.  With
 // w.gate set, every step but the fill runs only when *w.gate != 0 (list
 // reuse); the fill always rewrites the sorted positions from w.xw.
-// bsum must hold nblk(ncells, 1024) ints; rk_tab holds k2*Rcov per type (bohr).
+// bsum must hold nblk(ncells, 1024) ints; rk_tab holds k2*Rcov per type (bohr);
+// lmarks (optional): two events recorded around the list-builder kernel.
 cudaError_t launch_build_impl(const Work& w, const double* pos, const int32_t* types, const double* rk_tab,
-                              int* bsum, cudaStream_t st) {
+                              int* bsum, cudaStream_t st, cudaEvent_t* lmarks) {
     if (w.Nr == 0) return cudaGetLastError();
     const int TB = 256;
     const int64_t nreset = std::max<int64_t>(w.ncells + 1, 3 * (int64_t)w.B);
@@ -886,12 +887,14 @@ cudaError_t launch_build_impl(const Work& w, const double* pos, const int32_t* t
         // (per-atom lists) and per cluster (cluster lists)
         const int chunks = (int)((w.Nr + 31) / 32);
         const int blocks = std::min((chunks + 3) / 4, w.num_sms * w.build_per_sm);
+        if (lmarks) cudaEventRecord(lmarks[0], st);
         if (w.cl_mode) {  // cluster lists and, in the same walk, the per-atom CN lists
             const int bcl = (int)std::min<int64_t>((w.ncl + 3) / 4, (int64_t)w.num_sms * w.build_per_sm);
             if (w.ncl > 0) k_build_clist<<<bcl, 128, 0, st>>>(w);
         } else {
             k_build_lists<<<blocks, 128, 0, st>>>(w);
         }
+        if (lmarks) cudaEventRecord(lmarks[1], st);
     }
     return cudaGetLastError();
 }

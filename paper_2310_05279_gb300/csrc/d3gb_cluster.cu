@@ -61,9 +61,9 @@ __device__ __forceinline__ void red_add(unsigned long long* a, unsigned long lon
     if (x) atomicAdd(a, x);  // result unused: a reduction, no return trip
 }
 
-// Rows of v and dv for the image atoms: copies of their source atom's rows, so
-// that the pass reads every neighbour's data at the neighbour's own index (one
-// level of dependent loads per step).  rows = T * 2 * RP floats per atom.
+// Rows of v and dv for the image atoms, copies of their source atom's rows (used
+// when images x types is small against the real atoms), so that the pass reads a
+// neighbour's data at the neighbour's own index.  rows = T * 2 * RP floats per atom.
 __global__ void __launch_bounds__(256) k_vd_images(Work w, int rows) {
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= w.start_ghost[w.ncells]) return;
@@ -74,8 +74,9 @@ __global__ void __launch_bounds__(256) k_vd_images(Work w, int rows) {
     for (int k = 0; k < rows / 4; ++k) to[k] = __ldg(from + k);
 }
 
-// Data of one list entry for the lane's step: the neighbour's split position
-// and its rows v^(t_i), dv^(t_i); q = -1 past the end of the list.
+// Data of one list entry for the lane's step: the neighbour's split position and
+// its rows v^(t_i), dv^(t_i) (its own, or its source atom's); q = -1 past the end
+// of the list.
 template <int R>
 struct JData {
     float4 h, l;
@@ -84,11 +85,11 @@ struct JData {
 };
 
 template <int R>
-__device__ __forceinline__ void load_j(const Work& w, const float* __restrict__ vdb, int rows, int q, JData<R>& J) {
+__device__ __forceinline__ void load_j(const Work& w, const float* __restrict__ vdb, int rows, int q, int src,
+                                       JData<R>& J) {
     J.q = q;
-    const int64_t qq = q >= 0 ? q : 0;
-    rec_load(w, qq, J.h, J.l);
-    const float* r = vdb + qq * rows;
+    rec_load(w, q >= 0 ? q : 0, J.h, J.l);
+    const float* r = vdb + (int64_t)(src >= 0 ? src : 0) * rows;
     load_vec<R>(r, J.v);
     load_vec<R>(r + (R <= 4 ? 4 : 8), J.dv);
 }
@@ -107,6 +108,7 @@ struct ClusterPass {
     int b0, b1, il, fshift;
     unsigned long long* acc;
     int* status;
+    unsigned npairs = 0;  // used pairs of the warp (warp-uniform)
     // running sums of the lane's i
     float fx = 0.f, fy = 0.f, fz = 0.f;
     float dnc = 0.f, dnh = 0.f, dnl = 0.f;            // dE/dn_i: chunk partial and compensated sum
@@ -198,6 +200,7 @@ struct ClusterPass {
         }
         const unsigned uma = __ballot_sync(0xffffffffu, ause), umb = __ballot_sync(0xffffffffu, buse);
         if ((uma | umb) == 0u) return;
+        npairs += __popc(uma) + __popc(umb);
         float atx, aty, atz, adn, ae, btx, bty, btz, bdn, be;
         pair(A, ax, ay, az, ar2, ause, atx, aty, atz, adn, ae);
         pair(B, bx, by, bz, br2, buse, btx, bty, btz, bdn, be);
@@ -206,7 +209,9 @@ struct ClusterPass {
     }
 };
 
-template <int R, bool SITE>
+// IMGSRC: image atoms have no rows of their own; each list entry's source atom is
+// resolved once per block of 32 entries (from the image's compact record).
+template <int R, bool SITE, bool IMGSRC>
 __global__ void __launch_bounds__(128) k_disp_cl(Work w, Consts c, const float4* __restrict__ pair_tab) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float4* tab = reinterpret_cast<float4*>(smem_raw);
@@ -244,34 +249,50 @@ __global__ void __launch_bounds__(128) k_disp_cl(Work w, Consts c, const float4*
     const int cnt = w.cnt_cl[I];
     const int nsteps = (cnt + 3) >> 2;
     // list entries of steps 8b..8b+7 come from one coalesced load (lane k holds
-    // entry 32b + k), a block ahead; the neighbour data of the next two steps is
-    // loaded while two steps compute
+    // entry 32b + k) together with the entry's source atom (itself for a real atom,
+    // from the image's compact record otherwise), a block ahead; the neighbour data
+    // of the next two steps is loaded while two steps compute
+    const int nr = (int)w.Nr;
+    auto src_of = [&](int q) { return IMGSRC && q >= nr ? (__float_as_int(__ldg(&w.hi[q].w)) >> 4) : q; };
     int qa = lane < cnt ? __ldg(row + lane) : -1;
     int qb = 32 + lane < cnt ? __ldg(row + 32 + lane) : -1;
+    int sa = src_of(qa), sb = src_of(qb);
+    int eq = -1, es = -1;  // entry of the current call of entry()
     auto entry = [&](int t) {  // this lane's list entry of step t (called with t = 0, 1, 2, ... in order)
         if (t > 0 && (t & 7) == 0) {
             qa = qb;
+            sa = sb;
             const int k = 32 * ((t >> 3) + 1) + lane;
             qb = k < cnt ? __ldg(row + k) : -1;
+            sb = src_of(qb);
         }
-        return __shfl_sync(0xffffffffu, qa, ((t & 7) << 2) + js);
+        const int from = ((t & 7) << 2) + js;
+        eq = __shfl_sync(0xffffffffu, qa, from);
+        es = IMGSRC ? __shfl_sync(0xffffffffu, sa, from) : eq;
     };
     // steps in pairs: the data of steps t, t + 1 is in A, B while t + 2, t + 3 load into
     // C, D (past the end of the list the entries are -1: unused, no flush)
     JData<R> A, B, C, D;
-    load_j<R>(w, vdb, rows, entry(0), A);
-    load_j<R>(w, vdb, rows, entry(1), B);
+    entry(0);
+    load_j<R>(w, vdb, rows, eq, es, A);
+    entry(1);
+    load_j<R>(w, vdb, rows, eq, es, B);
     for (int t = 0; t < nsteps; t += 4) {
-        load_j<R>(w, vdb, rows, entry(t + 2), C);
-        load_j<R>(w, vdb, rows, entry(t + 3), D);
+        entry(t + 2);
+        load_j<R>(w, vdb, rows, eq, es, C);
+        entry(t + 3);
+        load_j<R>(w, vdb, rows, eq, es, D);
         P.step2(A, B);
         if (t + 2 >= nsteps) break;
-        load_j<R>(w, vdb, rows, entry(t + 4), A);
-        load_j<R>(w, vdb, rows, entry(t + 5), B);
+        entry(t + 4);
+        load_j<R>(w, vdb, rows, eq, es, A);
+        entry(t + 5);
+        load_j<R>(w, vdb, rows, eq, es, B);
         P.step2(C, D);
         if ((t & 12) == 12) P.chunk();  // every 16 steps
     }
     P.chunk();
+    if (lane == 0 && w.npairs) atomicAdd(w.npairs, (unsigned long long)P.npairs);
     // i side: sum the 4 lanes of each i (fixed order) and add to the accumulators
     float fx = P.fx, fy = P.fy, fz = P.fz, dnh = P.dnh, dnl = P.dnl, Eh = P.Eh, El = P.El;
 #pragma unroll
@@ -338,15 +359,20 @@ inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
 cudaError_t launch_disp_cl(const Work& w, const Consts& c, const void* pair_tab, bool site, cudaStream_t st) {
     if (w.Nr == 0) return cudaGetLastError();
-    if (w.ghost_cap > 0) k_vd_images<<<nblk(w.ghost_cap, 256), 256, 0, st>>>(w, c.T * 2 * c.RP);
+    if (w.vd_images) k_vd_images<<<nblk(w.ghost_cap, 256), 256, 0, st>>>(w, c.T * 2 * c.RP);
     if (w.ncl > 0) {
         const int TB = w.blk_disp;  // 64 or 128 threads: 2 or 4 clusters per block
         const unsigned grid = nblk(w.ncl, TB / 32);
         const size_t sm = (size_t)c.T * c.T * sizeof(float4);
         const float4* pt = (const float4*)pair_tab;
-#define D3_CL(RR)                                                              \
-    if (site) k_disp_cl<RR, true><<<grid, TB, sm, st>>>(w, c, pt);            \
-    else k_disp_cl<RR, false><<<grid, TB, sm, st>>>(w, c, pt);                \
+#define D3_CL(RR)                                                                  \
+    if (w.vd_images) {                                                             \
+        if (site) k_disp_cl<RR, true, false><<<grid, TB, sm, st>>>(w, c, pt);     \
+        else k_disp_cl<RR, false, false><<<grid, TB, sm, st>>>(w, c, pt);         \
+    } else {                                                                       \
+        if (site) k_disp_cl<RR, true, true><<<grid, TB, sm, st>>>(w, c, pt);      \
+        else k_disp_cl<RR, false, true><<<grid, TB, sm, st>>>(w, c, pt);          \
+    }                                                                              \
     break
         switch (c.R) {
             case 1: D3_CL(1);

@@ -153,9 +153,11 @@ struct Work {
     int* nbr_cl;             // rows of cap_cl entries per cluster
     int* cnt_cl;             // [ncl]
     unsigned long long* acc; // [Nr][8] fixed-point sums of the dispersion pass: F (3), dE/dn, site energy
-    float* vd;               // [Nr + ghost_cap][T][2][RP] per atom q (images included, copied from their
-                             // source) and partner type t: v_q^(t) and dv_q^(t)_a = sum_b C6ref[t][tq][a][b] dW_qb
+    float* vd;               // [Nr (+ ghost_cap)][T][2][RP] per atom q and partner type t: v_q^(t) and
+                             // dv_q^(t)_a = sum_b C6ref[t][tq][a][b] dW_qb
+    int vd_images;           // 1: image atoms have rows (copies of their source's), 0: they use their source's
     float* skey;             // [Nr] within-cell sort key (position along the serpentine direction), input order
+    unsigned long long* npairs;  // [1] unique pairs within R_pot of the last cluster-mode dispersion pass
     // list reuse (skin > 0): the build kernels run only while *gate != 0
     int* gate;               // nullptr: unconditional build; else set by k_check when an atom moved > skin/2
     double* xref;            // [Nr*3] positions (bohr, input order) at the last build
@@ -296,7 +298,8 @@ cudaError_t launch_atm(const Work& w, const Consts& c, bool mixed, const void* r
 // Eq. 8 per atom: J_i = W_i . v_i (device arrays).
 cudaError_t launch_heat(int64_t n, const double* w_atom, const double* vel, double* J, cudaStream_t st);
 constexpr int kForwardLaunches = 5;  // kernels per forward pass (B > 0, N > 0): CN, dispersion, chain, 2 sums
-                                     // (one more with the three-body term, one more in cluster mode)
+                                     // (one more with the three-body term; in cluster mode one more,
+                                     // the fixed-point finish, and a second for image rows of v, dv)
 constexpr int kBuildLaunches = 15;   // kernels per neighbour build (N > 0): reset, wrap, images, 2 x 3 scan,
-                                     // 2 scatter, sort, 2 fill, lists (one more in cluster mode)
+                                     // 2 scatter, sort, 2 fill, lists (per-atom or cluster lists)
 }  // namespace d3gb

@@ -102,6 +102,7 @@ __device__ __forceinline__ void store_weights(const Work& w, const Consts& c, co
             store_row<T>(dvp + (2 * u + 1) * c.RP, dvr, c.RP);
         }
     }
+    if (p == 0 && w.npairs) *w.npairs = 0ull;  // pair count of this call's dispersion pass
     if (w.acc) {  // clear the atom's fixed-point sums of the cluster-list dispersion pass
         ulonglong2* a = reinterpret_cast<ulonglong2*>(w.acc + 8 * p);
         const ulonglong2 z = make_ulonglong2(0ull, 0ull);

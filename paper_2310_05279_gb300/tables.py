@@ -175,3 +175,25 @@ def load_damping(path: str, functional: str) -> dict:
     if not all(math.isfinite(v) for v in out.values()):
         raise ValueError("non-finite damping parameter")
     return out
+
+
+def dftd3_params(spec, damping_path: str, k1: float = 16.0, k2: float = 4.0 / 3.0, k3: float = 4.0) -> dict:
+    """Library parameters from the method's three user inputs (Sec. II A: the
+    exchange-correlation functional, R_pot and R_cn), given either as an input
+    line ``"dftd3 <functional> <R_pot> <R_cn>"`` (cutoffs in A, e.g.
+    ``"dftd3 pbe 12 6"``) or as a tuple ``(functional, R_pot, R_cn)``.  The
+    functional's damping parameters come from ``damping_path`` (load_damping);
+    k1, k2, k3 are the constants of Eqs. 3-4.  Returns the dict ``D3`` takes."""
+    if isinstance(spec, str):
+        words = spec.split()
+        if len(words) != 4 or words[0].lower() != "dftd3":
+            raise ValueError(f"expected 'dftd3 <functional> <R_pot> <R_cn>', got {spec!r}")
+        functional, rpot, rcn = words[1], words[2], words[3]
+    else:
+        functional, rpot, rcn = spec
+    rpot, rcn = float(rpot), float(rcn)
+    if not (math.isfinite(rpot) and math.isfinite(rcn) and rpot > 0 and rcn > 0):
+        raise ValueError("cutoffs must be positive")
+    p = load_damping(damping_path, functional)
+    return dict(p, k1=float(k1), k2=float(k2), k3=float(k3), rc_disp=rpot, rc_cn=rcn)
+

@@ -124,3 +124,48 @@ def test_mixed_backward_vs_fp64_full_fit_batch(setup):
     m, f = res["mixed"], res["fp64"]
     assert np.all(np.abs(m["dparams"] - f["dparams"]) <= 1e-6 * np.abs(f["dparams"]))
     assert np.abs(m["dpos"] - f["dpos"]).max() <= 1e-6 * np.abs(f["dpos"]).max()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_fit_batch_sizes_vs_oracle_gradient(oracle_mod, precision):
+    """Structures of the fit batch's size range (200-2000 atoms) against the oracle's
+    gradient: dL/dtheta from its analytic dE/dtheta and central differences of its
+    analytic forces in theta, dL/dx on a stated subset of 6 coordinates by central
+    differences of the oracle's loss."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    b = wl.fit_batch(seed=43, nstruct=3, n_range=(200, 2000))
+    assert np.diff(b.offsets).min() >= 200
+    tgt = wl.perturbed_damping(5)
+    ref = oracle_mod.compute_batch(b, tgt)
+    Et, Ft = ref["E"], ref["F"]
+    prm = dict(wl.PBE_BJ)
+    gp, gx = gpu_grad(torch, b, prm, Et, Ft, precision)
+    L0, r0 = oracle_loss(oracle_mod, b, prm, Et, Ft)
+    gE = 2.0 * (r0["E"] - Et)
+    gF = 2.0 * LAM * (r0["F"] - Ft)
+    og = np.zeros(4)
+    for k, name in enumerate(["s6", "s8", "a1", "a2"]):
+        h = 1e-5
+        pp, pm = dict(prm), dict(prm)
+        pp[name] += h
+        pm[name] -= h
+        rp = oracle_mod.compute_batch(b, pp)
+        rm = oracle_mod.compute_batch(b, pm)
+        og[k] = np.dot(gE, r0["dEdp"][:, k]) + np.sum(gF * (rp["F"] - rm["F"]) / (2 * h))
+    np.testing.assert_allclose(gp, og, rtol=1e-6, atol=1e-9 * np.abs(og).max())
+    g = np.random.Generator(np.random.PCG64(7))
+    for i in g.choice(b.natoms, 6, replace=False):
+        a = int(g.integers(0, 3))
+        s = int(np.searchsorted(b.offsets, i, side="right") - 1)
+        sl = slice(int(b.offsets[s]), int(b.offsets[s + 1]))
+        h = 1e-5
+        bp = wl.Batch(b.pos.copy(), b.types, b.offsets, b.cells, b.pbc, b.tables)
+        bm = wl.Batch(b.pos.copy(), b.types, b.offsets, b.cells, b.pbc, b.tables)
+        bp.pos[i, a] += h
+        bm.pos[i, a] -= h
+        Lp, _ = oracle_loss(oracle_mod, bp.subset([s]), prm, Et[[s]], Ft[sl])
+        Lm, _ = oracle_loss(oracle_mod, bm.subset([s]), prm, Et[[s]], Ft[sl])
+        fd = (Lp - Lm) / (2 * h)
+        assert abs(gx[i, a] - fd) <= 1e-5 * max(1.0, abs(fd)), (i, a, gx[i, a], fd)

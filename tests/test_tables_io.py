@@ -76,3 +76,22 @@ def test_damping_file(tmp_path):
     q.write_text(json.dumps({"format": "something-else"}))
     with pytest.raises(ValueError):
         tio.load_damping(str(q), "pbe")
+
+
+def test_dftd3_input_line(tmp_path):
+    """The paper's three inputs (functional, R_pot, R_cn) as an input line or a tuple."""
+    p = str(tmp_path / "d.json")
+    json.dump({"format": tio.DAMPING_FORMAT, "functionals": {
+        "PBE": {"s6": 1.0, "s8": 0.7875, "a1": 0.4289, "a2_bohr": 4.4407},
+        "other": {"s6": 1.0, "s8": 0.9, "a1": 0.5, "a2_bohr": 4.0}}}, open(p, "w"))
+    a = tio.dftd3_params("dftd3 pbe 12 6", p)
+    assert a == dict(s6=1.0, s8=0.7875, a1=0.4289, a2=4.4407, k1=16.0, k2=4.0 / 3.0, k3=4.0, rc_disp=12.0, rc_cn=6.0)
+    b = tio.dftd3_params(("OTHER", 20, 10.5), p)
+    assert (b["s8"], b["a1"], b["a2"], b["rc_disp"], b["rc_cn"]) == (0.9, 0.5, 4.0, 20.0, 10.5)
+    with pytest.raises(ValueError):
+        tio.dftd3_params("dftd3 pbe 12", p)
+    with pytest.raises(ValueError):
+        tio.dftd3_params("dftd3 pbe -1 6", p)
+    with pytest.raises(KeyError):
+        tio.dftd3_params("dftd3 b3lyp 12 6", p)
+

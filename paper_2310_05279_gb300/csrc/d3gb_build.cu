@@ -709,7 +709,9 @@ __global__ void __launch_bounds__(128) k_build_lists(Work w) {
 // flattened: 32 ranges at a time, their lengths scanned across the lanes, then
 // 32 candidates at a time, each lane finding its range by a binary search over
 // the scanned offsets held in the lanes.  Candidates are appended in walk
-// order (ballot compaction), so every list is deterministic.
+// order (ballot compaction), so every list is deterministic.  Candidates within
+// the CN list radius of the bounding box are first staged in shared memory, in
+// walk order, and tested against the cluster's atoms 32 at a time.
 __global__ void __launch_bounds__(128) k_build_clist(Work w) {
     if (skip_build(w)) return;
     const int lane = threadIdx.x & 31;
@@ -718,7 +720,11 @@ __global__ void __launch_bounds__(128) k_build_clist(Work w) {
     const float4* __restrict__ H = w.hi;
     const int zero_shift = pack_shift(0, 0, 0);
     __shared__ float4 sh_i[4][kClusterAtoms];  // the cluster's atoms (hi positions) per warp
+    __shared__ float4 sh_ch[4][64];            // staged CN candidates per warp: position, index
+    __shared__ int sh_cq[4][64];
     float4* hi8 = sh_i[threadIdx.x >> 5];
+    float4* ch = sh_ch[threadIdx.x >> 5];
+    int* cq = sh_cq[threadIdx.x >> 5];
     for (;;) {
         const int64_t I = next_chunk(w, lane, 1);
         if (I >= w.ncl) return;
@@ -754,6 +760,40 @@ __global__ void __launch_bounds__(128) k_build_clist(Work w) {
         const int first = (int)p0, last = (int)p0 + nI;  // the cluster's own sorted slots
         int n = 0;
         int nc[kClusterAtoms] = {0, 0, 0, 0, 0, 0, 0, 0};  // CN list lengths (warp-uniform)
+        int ns = 0;                                        // staged CN candidates (warp-uniform)
+        // per-atom CN lists of the cluster's atoms from the first m staged candidates
+        auto cn_round = [&](int m) {
+            __syncwarp();
+            const bool live = lane < m;
+            const int q = live ? cq[lane] : -1;
+            const float4 hq = ch[lane];
+#pragma unroll
+            for (int i = 0; i < kClusterAtoms; ++i) {
+                if (i >= nI) break;
+                const float4 hp = hi8[i];
+                const float dx = hq.x - hp.x, dy = hq.y - hp.y, dz = hq.z - hp.z;
+                const bool in = live && q != first + i && fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < rn2;
+                const unsigned mi = __ballot_sync(full, in);
+                const int kc = nc[i] + __popc(mi & ((1u << lane) - 1u));
+                if (in && kc < capc) w.nbr_cn[list_row(G.list_base_cn, (int64_t)first + i - G.atom_base, capc) + kc] = q;
+                nc[i] += __popc(mi);
+            }
+            // move the rest (fewer than 32) to the front
+            const int rest = ns - m;
+            float4 h2 = make_float4(0.f, 0.f, 0.f, 0.f);
+            int q2 = 0;
+            if (lane < rest) {
+                h2 = ch[m + lane];
+                q2 = cq[m + lane];
+            }
+            __syncwarp();
+            if (lane < rest) {
+                ch[lane] = h2;
+                cq[lane] = q2;
+            }
+            ns = rest;
+            __syncwarp();
+        };
         for (int r0 = 0; r0 < nranges; r0 += 32) {
             // this lane's range: row (y, z) = (r / 2) and real (r even) or image atoms
             int b = 0, len = 0;
@@ -812,25 +852,18 @@ __global__ void __launch_bounds__(128) k_build_clist(Work w) {
                 const int kk = n + __popc(m & ((1u << lane) - 1u));
                 if (take && kk < cap) row[kk] = q;
                 n += __popc(m);
-                // per-atom CN lists of the cluster's atoms
-                if (__any_sync(full, cn_cand)) {
-#pragma unroll
-                    for (int i = 0; i < kClusterAtoms; ++i) {
-                        if (i >= nI) break;
-                        const float4 hp = hi8[i];
-                        const float dx = hq.x - hp.x, dy = hq.y - hp.y, dz = hq.z - hp.z;
-                        const bool in = cn_cand && q != first + i && fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < rn2;
-                        const unsigned mi = __ballot_sync(full, in);
-                        if (mi) {
-                            const int kc = nc[i] + __popc(mi & ((1u << lane) - 1u));
-                            if (in && kc < capc)
-                                w.nbr_cn[list_row(G.list_base_cn, (int64_t)first + i - G.atom_base, capc) + kc] = q;
-                            nc[i] += __popc(mi);
-                        }
-                    }
+                // stage the CN candidates in walk order
+                const unsigned mcn = __ballot_sync(full, cn_cand);
+                if (cn_cand) {
+                    const int kk2 = ns + __popc(mcn & ((1u << lane) - 1u));
+                    ch[kk2] = hq;
+                    cq[kk2] = q;
                 }
+                ns += __popc(mcn);
+                if (ns >= 32) cn_round(32);
             }
         }
+        if (ns > 0) cn_round(ns);
         int mc = 0;
 #pragma unroll
         for (int i = 0; i < kClusterAtoms; ++i)

@@ -34,17 +34,15 @@ constexpr double kUnfix = 1.0 / 1099511627776.0;  // Hartree (or Hartree/bohr) p
 // additions and integer operations only (conversions from FP32 to integers run on
 // the FP64 pipe of this GPU): v 2^40 = h 2^32 + m 2^16 + n with each of h, m, n
 // rounded by the 1.5 2^23 trick (exact for magnitudes below 2^22) and every
-// remainder formed exactly.  A larger (or non-finite) |v| sets ST_SUM_RANGE.
+// remainder formed exactly.  A larger (or non-finite) |v| sets the flag bad (the
+// caller turns it into ST_SUM_RANGE; the returned value is then meaningless).
 __device__ __forceinline__ int magic_rint(float x, float& xr) {  // rint(x) for |x| < 2^22, and its float value
     const float f = x + 12582912.0f;
     xr = f - 12582912.0f;
     return __float_as_int(f) - 0x4B400000;
 }
-__device__ __forceinline__ unsigned long long fix40(float v, int* status) {
-    if (!(fabsf(v) < 16384.0f)) {
-        atomicOr(status, ST_SUM_RANGE);
-        return 0ull;
-    }
+__device__ __forceinline__ unsigned long long fix40(float v, bool& bad) {
+    bad |= !(fabsf(v) < 16384.0f);
     float hr, mr;
     const float a = v * 256.0f;                       // v 2^8
     const int h = magic_rint(a, hr);
@@ -58,7 +56,12 @@ __device__ __forceinline__ unsigned long long fix40(float v, int* status) {
 }
 
 __device__ __forceinline__ void red_add(unsigned long long* a, unsigned long long x) {
-    if (x) atomicAdd(a, x);  // result unused: a reduction, no return trip
+    atomicAdd(a, x);  // result unused: a reduction, no return trip
+}
+// the same under a predicate, without a branch around it
+__device__ __forceinline__ void red_add_if(bool p, unsigned long long* a, unsigned long long x) {
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q red.relaxed.gpu.global.add.u64 [%0], %1;\n\t}"
+                 :: "l"(a), "l"(x), "r"((unsigned)p) : "memory");
 }
 
 // Rows of v and dv for the image atoms, copies of their source atom's rows (used
@@ -107,7 +110,7 @@ struct ClusterPass {
     double rc2d;
     int b0, b1, il, fshift;
     unsigned long long* acc;
-    int* status;
+    bool bad = false;     // a fixed-point value out of range (ST_SUM_RANGE at the end)
     unsigned npairs = 0;  // used pairs of the warp (warp-uniform)
     // running sums of the lane's i
     float fx = 0.f, fy = 0.f, fz = 0.f;
@@ -185,8 +188,9 @@ struct ClusterPass {
             ej += __shfl_xor_sync(0xffffffffu, ej, 4);
             if (il == 4) mv = ej;
         }
-        if (il < (SITE ? 5 : 4) && ((um >> fshift) & 0xffu))  // some pair of this j was used
-            red_add(acc + 8 * (int64_t)(tsq >> 4) + (il < 4 ? 2 * b0 + b1 : 4), fix40(mv, status));
+        const unsigned long long x = fix40(mv, bad);
+        red_add_if(il < (SITE ? 5 : 4) && ((um >> fshift) & 0xffu),  // some pair of this j was used
+                   acc + 8 * (int64_t)(tsq >> 4) + (il < 4 ? 2 * b0 + b1 : 4), x);
     }
 
     __device__ __forceinline__ void step2(const JData<R>& A, const JData<R>& B) {
@@ -211,8 +215,10 @@ struct ClusterPass {
 
 // IMGSRC: image atoms have no rows of their own; each list entry's source atom is
 // resolved once per block of 32 entries (from the image's compact record).
+// The bound (128, 3) holds every instantiation to 168 registers, so that three
+// 128-thread blocks (12 warps) stay resident per SM whatever R is.
 template <int R, bool SITE, bool IMGSRC>
-__global__ void __launch_bounds__(128) k_disp_cl(Work w, Consts c, const float4* __restrict__ pair_tab) {
+__global__ void __launch_bounds__(128, 3) k_disp_cl(Work w, Consts c, const float4* __restrict__ pair_tab) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float4* tab = reinterpret_cast<float4*>(smem_raw);
     for (int k = threadIdx.x; k < c.T * c.T; k += blockDim.x) tab[k] = pair_tab[k];
@@ -241,55 +247,53 @@ __global__ void __launch_bounds__(128) k_disp_cl(Work w, Consts c, const float4*
     P.il = il;
     P.fshift = lane & 24;
     P.acc = w.acc;
-    P.status = w.status;
     constexpr int RPc = R <= 4 ? 4 : 8;
     const int rows = c.T * 2 * RPc;          // floats of v/dv rows per atom
     const float* vdb = w.vd + ti * 2 * RPc;  // the rows for partner type t_i
     const int* row = w.nbr_cl + G.list_base_cl + (I - G.clu_base) * (int64_t)G.cap_cl;
     const int cnt = w.cnt_cl[I];
     const int nsteps = (cnt + 3) >> 2;
-    // list entries of steps 8b..8b+7 come from one coalesced load (lane k holds
-    // entry 32b + k) together with the entry's source atom (itself for a real atom,
-    // from the image's compact record otherwise), a block ahead; the neighbour data
-    // of the next two steps is loaded while two steps compute
+    // list entries of steps 8b..8b+7 (block b) come from one coalesced load, lane k
+    // holding entry 32b + k, together with the entry's source atom (itself for a real
+    // atom; with IMGSRC, an image's source from its compact record), a block ahead.
+    // The neighbour data of the next two steps is loaded while two steps compute.
+    // Whole blocks are processed: entries past the end of the list are -1 (unused).
     const int nr = (int)w.Nr;
     auto src_of = [&](int q) { return IMGSRC && q >= nr ? (__float_as_int(__ldg(&w.hi[q].w)) >> 4) : q; };
     int qa = lane < cnt ? __ldg(row + lane) : -1;
     int qb = 32 + lane < cnt ? __ldg(row + 32 + lane) : -1;
     int sa = src_of(qa), sb = src_of(qb);
-    int eq = -1, es = -1;  // entry of the current call of entry()
-    auto entry = [&](int t) {  // this lane's list entry of step t (called with t = 0, 1, 2, ... in order)
-        if (t > 0 && (t & 7) == 0) {
-            qa = qb;
-            sa = sb;
-            const int k = 32 * ((t >> 3) + 1) + lane;
-            qb = k < cnt ? __ldg(row + k) : -1;
-            sb = src_of(qb);
-        }
-        const int from = ((t & 7) << 2) + js;
-        eq = __shfl_sync(0xffffffffu, qa, from);
-        es = IMGSRC ? __shfl_sync(0xffffffffu, sa, from) : eq;
+    // this lane's entry of step s (0..7) of the current block
+    auto load = [&](int st, JData<R>& J) {
+        const int from = (st << 2) + js;
+        const int q = __shfl_sync(0xffffffffu, qa, from);
+        const int src = IMGSRC ? __shfl_sync(0xffffffffu, sa, from) : q;
+        load_j<R>(w, vdb, rows, q, src, J);
     };
-    // steps in pairs: the data of steps t, t + 1 is in A, B while t + 2, t + 3 load into
-    // C, D (past the end of the list the entries are -1: unused, no flush)
     JData<R> A, B, C, D;
-    entry(0);
-    load_j<R>(w, vdb, rows, eq, es, A);
-    entry(1);
-    load_j<R>(w, vdb, rows, eq, es, B);
-    for (int t = 0; t < nsteps; t += 4) {
-        entry(t + 2);
-        load_j<R>(w, vdb, rows, eq, es, C);
-        entry(t + 3);
-        load_j<R>(w, vdb, rows, eq, es, D);
+    load(0, A);
+    load(1, B);
+    const int nblocks = (nsteps + 7) >> 3;
+    for (int b = 0; b < nblocks; ++b) {
+        load(2, C);
+        load(3, D);
         P.step2(A, B);
-        if (t + 2 >= nsteps) break;
-        entry(t + 4);
-        load_j<R>(w, vdb, rows, eq, es, A);
-        entry(t + 5);
-        load_j<R>(w, vdb, rows, eq, es, B);
+        load(4, A);
+        load(5, B);
         P.step2(C, D);
-        if ((t & 12) == 12) P.chunk();  // every 16 steps
+        load(6, C);
+        load(7, D);
+        P.step2(A, B);
+        // next block: its entries become current, the one after is loaded
+        qa = qb;
+        sa = sb;
+        const int k = 32 * (b + 2) + lane;
+        qb = k < cnt ? __ldg(row + k) : -1;
+        sb = src_of(qb);
+        load(0, A);
+        load(1, B);
+        P.step2(C, D);
+        if (b & 1) P.chunk();  // every 16 steps
     }
     P.chunk();
     if (lane == 0 && w.npairs) atomicAdd(w.npairs, (unsigned long long)P.npairs);
@@ -310,12 +314,13 @@ __global__ void __launch_bounds__(128) k_disp_cl(Work w, Consts c, const float4*
     unsigned long long* acc = w.acc;
     if (js == 0 && ilive) {
         unsigned long long* ai = acc + 8 * p;
-        red_add(ai + 0, fix40(fx, w.status));
-        red_add(ai + 1, fix40(fy, w.status));
-        red_add(ai + 2, fix40(fz, w.status));
-        red_add(ai + 3, fix40(dnh, w.status) + fix40(dnl, w.status));
-        if (SITE) red_add(ai + 4, fix40(Eh, w.status) + fix40(El, w.status));
+        red_add(ai + 0, fix40(fx, P.bad));
+        red_add(ai + 1, fix40(fy, P.bad));
+        red_add(ai + 2, fix40(fz, P.bad));
+        red_add(ai + 3, fix40(dnh, P.bad) + fix40(dnl, P.bad));
+        if (SITE) red_add(ai + 4, fix40(Eh, P.bad) + fix40(El, P.bad));
     }
+    if (P.bad) atomicOr(w.status, ST_SUM_RANGE);
     // the cluster's virial, -sum_pairs fc d (x) d (the partials are of nfc d (x) d), and
     // without SITE its energy, in FP64 on its first atom (the per-structure sums use
     // them); zero on the others

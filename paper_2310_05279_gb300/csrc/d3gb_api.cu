@@ -456,6 +456,7 @@ d3_status plan_alloc(d3_handle* h, Plan& P) {
     // rows of v and dv for real and image atoms (whether images get copies of their
     // source's rows is decided after the sizing pass, from the image count)
     if (h->prm.precision == D3_MIXED) A(w.vd, float, Nt * h->T * 2 * h->RP);
+    if (h->prm.precision == D3_MIXED) A(w.gcn, float, lc);
     A(w.gate, int, 1);
     A(w.xref, double, 3 * Nr);
     A(w.wshift, double, 3 * Nr);

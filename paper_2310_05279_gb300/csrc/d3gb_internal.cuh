@@ -153,6 +153,8 @@ struct Work {
     int* nbr_cl;             // rows of cap_cl entries per cluster
     int* cnt_cl;             // [ncl]
     unsigned long long* acc; // [Nr][8] fixed-point sums of the dispersion pass: F (3), dE/dn, site energy
+    float* gcn;              // mixed form: per CN-list entry, the chain coefficient f'(r)/r of Eq. 4
+                             // (written by the CN pass, 0 outside R_cn; read by the chain pass)
     float* vd;               // [Nr (+ ghost_cap)][T][2][RP] per atom q and partner type t: v_q^(t) and
                              // dv_q^(t)_a = sum_b C6ref[t][tq][a][b] dW_qb
     int vd_images;           // 1: image atoms have rows (copies of their source's), 0: they use their source's

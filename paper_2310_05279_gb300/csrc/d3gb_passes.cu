@@ -228,7 +228,10 @@ __device__ __forceinline__ void weights_atom_mixed(const Work& w, const Consts& 
 // keeps n_i accurate to a few 1e-8: the pair vector is exact (D + e), r^2 is
 // formed in double-single, the argument k1 (rc/r - 1) is evaluated as
 // k1 (rc^2 - r^2) / (r (rc + r)) so its error is relative to its own size,
-// and the sum over neighbours is compensated.
+// and the sum over neighbours is compensated.  The mixed form also stores, per
+// list entry, the chain-rule coefficient f'(r)/r of the pair (0 outside R_cn),
+// which depends on the geometry only: the chain pass reads it instead of forming
+// the double-single Eq. 4 term a second time.
 template <bool MIXED, int R>
 __global__ void __launch_bounds__(128) k_cn(Work w, Consts c, const float4* __restrict__ rcpair,
                                            const float2* __restrict__ exptab, const double* __restrict__ cnref,
@@ -247,10 +250,12 @@ __global__ void __launch_bounds__(128) k_cn(Work w, Consts c, const float4* __re
     if constexpr (MIXED) {
         const float4* rrow = rcpair + (S.tsrc() & 15) * c.T;
         int nint = 0;  // terms with f > 1/2 are summed as 1 - t/(1 + t): exact integer part plus a small complement
-        LV.for_each(0, cnt, [&](int q) {
-            float D[3], r2, ah, al, rch;
+        const int* row = LV.p;
+        float* grow = w.gcn + (row - w.nbr_cn);
+        auto term = [&](int q) -> float {  // the pair's CN term; returns f'(r)/r (0 outside R_cn)
+            float D[3], r2, ah, al, rch, rcl, r2l;
             int tq;
-            if (!cn_pair_precise(S, q, rrow, k1, rc2, c.rc_cn2, D, r2, ah, al, rch, tq)) return;
+            if (!cn_pair_precise(S, q, rrow, k1, rc2, c.rc_cn2, D, r2, ah, al, rch, tq, &rcl, &r2l)) return 0.0f;
             const CnDS z = cn_ds(ah, al, exptab);
             if (z.th < 1.0f) {
                 ++nint;
@@ -260,7 +265,17 @@ __global__ void __launch_bounds__(128) k_cn(Work w, Consts c, const float4* __re
                 acc_add(nh, nl, z.fh);
                 nl += z.fl;
             }
-        });
+            return chain_coef(z, r2, r2l, rch, rcl, k1);
+        };
+        for (int k = 0; k < cnt; k += 4) {
+            const int4 q4 = __ldg(reinterpret_cast<const int4*>(row + k));
+            float4 g4;
+            g4.x = term(q4.x);
+            g4.y = k + 1 < cnt ? term(q4.y) : 0.0f;
+            g4.z = k + 2 < cnt ? term(q4.z) : 0.0f;
+            g4.w = k + 3 < cnt ? term(q4.w) : 0.0f;
+            *reinterpret_cast<float4*>(grow + k) = g4;
+        }
         float Nh, Nl;  // n = nint + nh + nl as a float pair
         two_sum((float)nint, nh, Nh, Nl);
         Nl += nl;
@@ -401,17 +416,14 @@ __global__ void __launch_bounds__(128) k_chain(Work w, Consts c, const float4* _
         const int k1e = min(cnt, k0 + kChunk);
         T sxx = 0, syy = 0, szz = 0, sxy = 0, sxz = 0, syz = 0;
         T tm[6] = {0, 0, 0, 0, 0, 0}, gv[3] = {0, 0, 0}, mm[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-        LV.for_each(k0, k1e, [&](int q) {
-            T dx, dy, dz, g, dnq;
+        auto entry = [&](int q, T g) {
+            T dx, dy, dz, dnq;
             int srcq;
             if constexpr (MIXED) {
-                float D[3], r2, ah, al, rch, rcl, r2l;
+                if (g == 0.0f) return;  // outside R_cn (an exact zero adds nothing either)
+                float D[3], e[3];
                 int tq;
-                if (!cn_pair_precise(S, q, rcpair + (S.tsrc() & 15) * c.T, k1, rc2, c.rc_cn2, D, r2, ah, al, rch, tq,
-                                     &rcl, &r2l))
-                    return;
-                const CnDS z = cn_ds(ah, al, exptab);
-                g = chain_coef(z, r2, r2l, rch, rcl, k1);
+                S.dist_exact(q, D, e, tq);
                 srcq = tq >> 4;
                 dnq = dEdn[srcq];
                 dx = D[0]; dy = D[1]; dz = D[2];
@@ -444,7 +456,20 @@ __global__ void __launch_bounds__(128) k_chain(Work w, Consts c, const float4* _
                 mm[3] = fma(gb, dx, mm[3]); mm[4] = fma(gb, dy, mm[4]); mm[5] = fma(gb, dz, mm[5]);
                 mm[6] = fma(gc, dx, mm[6]); mm[7] = fma(gc, dy, mm[7]); mm[8] = fma(gc, dz, mm[8]);
             }
-        });
+        };
+        if constexpr (MIXED) {
+            const float* grow = w.gcn + (LV.p - w.nbr_cn);
+            for (int k = k0; k < k1e; k += 4) {
+                const int4 q4 = __ldg(reinterpret_cast<const int4*>(LV.p + k));
+                const float4 g4 = __ldg(reinterpret_cast<const float4*>(grow + k));
+                entry(q4.x, g4.x);  // entries past the end of the list have g = 0
+                entry(q4.y, g4.y);
+                entry(q4.z, g4.z);
+                entry(q4.w, g4.w);
+            }
+        } else {
+            LV.for_each(k0, k1e, [&](int q) { entry(q, (T)0); });
+        }
         Sxx += (double)sxx; Syy += (double)syy; Szz += (double)szz;
         Sxy += (double)sxy; Sxz += (double)sxz; Syz += (double)syz;
         if constexpr (ATOMV) {

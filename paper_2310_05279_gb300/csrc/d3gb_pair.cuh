@@ -210,8 +210,10 @@ __device__ __forceinline__ CnDS cn_ds(float ah, float al, const float2* __restri
     // x = -a, clamped so that 2^m stays a normal FP32 scale (|x| <= 87: t in [1.6e-38, 6e37])
     float xh = -ah, xl = -al;
     if (fabsf(xh) > 87.0f) { xh = copysignf(87.0f, xh); xl = 0.0f; }
-    const float kf = rintf(xh * kExpInvL);
-    const int k = (int)kf;
+    // k = rint(x/L) by the 1.5 2^23 trick (|x/L| < 2^13), from FP32 additions only
+    const float kb = __fmul_rn(xh, kExpInvL) + 12582912.0f;
+    const float kf = kb - 12582912.0f;
+    const int k = __float_as_int(kb) - 0x4B400000;
     const float r1 = fmaf(-kf, kExpL1, xh);  // exact (see kExpL1)
     const float p2 = kf * kExpL2, p2e = fmaf(kf, kExpL2, -p2);
     float rh, re;
@@ -219,15 +221,16 @@ __device__ __forceinline__ CnDS cn_ds(float ah, float al, const float2* __restri
     const float rl = ((re - p2e) - kf * kExpL3) + xl;
     // exp(r) - 1 = rh + s
     const float s = rl + rh * rl + rh * rh * fmaf(rh, fmaf(rh, 1.0f / 24.0f, 1.0f / 6.0f), 0.5f);
-    const int j = k & 63, m = (k - j) / 64;
+    const int j = k & 63, m = k >> 6;  // k = 64 m + j, |m| <= 126
     const float2 T = __ldg(tab + j);
     const float ph = T.x * rh, pe = fmaf(T.x, rh, -ph);
     const float hh = T.x + ph, he = ph - (hh - T.x);  // |T.x| >= |ph|: Fast2Sum
     const float lo = he + pe + T.y + fmaf(T.x, s, T.y * rh);
     float th = hh + lo;
     float tl = lo - (th - hh);
-    th = ldexpf(th, m);
-    tl = ldexpf(tl, m);
+    const float sc = __int_as_float((m + 127) << 23);  // 2^m, a normal FP32 number
+    th *= sc;
+    tl *= sc;
     CnDS o;
     o.th = th;
     o.tl = tl;

@@ -270,19 +270,28 @@ __device__ inline int block_exclusive_scan(int v, int* total) {
     return before + x - v;
 }
 
-__global__ void k_scan_blocks(const int* __restrict__ cnt, int* __restrict__ start, int* __restrict__ bsum,
-                              int64_t n, const int* gate) {
+// Two arrays at once (the real and the image counts per cell): array a = 0, 1 is
+// cnt[a] -> start[a], with its block sums at bsum + a nb.
+struct ScanPair {
+    const int* cnt[2];
+    int* start[2];
+};
+
+__global__ void k_scan_blocks(ScanPair sp, int* __restrict__ bsum, int nb, int64_t n, const int* gate) {
     if (gate && *gate == 0) return;
+    const int a = blockIdx.y;
     int64_t i = (int64_t)blockIdx.x * kScanBlock + threadIdx.x;
-    int v = i < n ? cnt[i] : 0;
+    int v = i < n ? sp.cnt[a][i] : 0;
     int tot;
     int ex = block_exclusive_scan(v, &tot);
-    if (i < n) start[i] = ex;
-    if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+    if (i < n) sp.start[a][i] = ex;
+    if (threadIdx.x == 0) bsum[a * nb + blockIdx.x] = tot;
 }
 
-__global__ void k_scan_sums(int* bsum, int nb, int* start, int64_t n, const int* gate) {
+__global__ void k_scan_sums(ScanPair sp, int* bsum_all, int nb, int64_t n, const int* gate) {
     if (gate && *gate == 0) return;
+    int* bsum = bsum_all + blockIdx.x * nb;
+    int* start = sp.start[blockIdx.x];
     int carry = 0;
     for (int base = 0; base < nb; base += kScanBlock) {
         int i = base + threadIdx.x;
@@ -296,25 +305,25 @@ __global__ void k_scan_sums(int* bsum, int nb, int* start, int64_t n, const int*
     if (threadIdx.x == 0) start[n] = carry;
 }
 
-__global__ void k_scan_add(int* start, const int* __restrict__ bsum, int64_t n, const int* gate) {
+__global__ void k_scan_add(ScanPair sp, const int* __restrict__ bsum, int nb, int64_t n, const int* gate) {
     if (gate && *gate == 0) return;
+    const int a = blockIdx.y;
     int64_t i = (int64_t)blockIdx.x * kScanBlock + threadIdx.x;
-    if (i < n) start[i] += bsum[blockIdx.x];
+    if (i < n) sp.start[a][i] += bsum[a * nb + blockIdx.x];
 }
 
-// ---- scatter into cell order
-__global__ void k_scatter_real(Work w) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= w.Nr || skip_build(w)) return;
-    w.sorted_src[w.start_real[w.cell_of[i]] + w.slot_of[i]] = (int)i;
-}
-
-__global__ void k_scatter_ghost(Work w) {
+// ---- scatter into cell order: threads [0, Nr) the real atoms, then the images
+__global__ void k_scatter(Work w) {
     if (skip_build(w)) return;
-    int g = blockIdx.x * blockDim.x + threadIdx.x;
-    int ng = min(*w.ghost_count, w.ghost_cap);
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < w.Nr) {
+        w.sorted_src[w.start_real[w.cell_of[i]] + w.slot_of[i]] = (int)i;
+        return;
+    }
+    const int64_t g = i - w.Nr;
+    const int ng = min(*w.ghost_count, w.ghost_cap);
     if (g >= ng) return;
-    w.gsorted[w.start_ghost[w.ghost_cell[g]] + w.ghost_slot[g]] = g;
+    w.gsorted[w.start_ghost[w.ghost_cell[g]] + w.ghost_slot[g]] = (int)g;
 }
 
 // Deterministic order inside each cell: real atoms by their position along the
@@ -324,7 +333,9 @@ __global__ void k_scatter_ghost(Work w) {
 // form one contiguous slice of sorted slots: the slice is staged in shared
 // memory, each thread insertion-sorts its own cell there, and the slice is
 // written back.  A slice larger than the stage is sorted in place in global
-// memory instead.
+// memory instead.  The sort also writes the inverse permutation of the real
+// atoms (slot_of[i] = sorted slot of input atom i; until then slot_of holds the
+// atoms' places in their cells, which the scatter has used).
 constexpr int kSortStage = 2048;
 
 __device__ __forceinline__ long long image_key(const Work& w, int g) {
@@ -386,11 +397,16 @@ __global__ void __launch_bounds__(256) k_sort_cells(Work w) {
                     }
                     w.sorted_src[m + 1] = i;
                 }
+                for (int k = b; k < e; ++k) w.slot_of[w.sorted_src[k]] = k;
             }
         }
         __syncthreads();
         if (fits)
-            for (int k = lo + threadIdx.x; k < hi; k += blockDim.x) w.sorted_src[k] = sr[k - lo];
+            for (int k = lo + threadIdx.x; k < hi; k += blockDim.x) {
+                const int i = sr[k - lo];
+                w.sorted_src[k] = i;
+                w.slot_of[i] = k;
+            }
         __syncthreads();  // sk is reused for the images below
     }
     {
@@ -487,9 +503,7 @@ __global__ void __launch_bounds__(256) k_check(Work w, const double* __restrict_
 // exact to 2^-24 |xh|) without FP64 products: m = rint(1024 xh), then the
 // remainder 1024 (xh - m/1024) + 1024 xl, exact in FP32 below 2^-10 by
 // Sterbenz, moves m by one when it exceeds 1/2.
-__device__ inline void store_pos(Work& w, int64_t q, const double x[3], double rk, int tsrc) {
-    w.pos64[q] = dbl4_make(x[0], x[1], x[2], rk);
-    float h[3], l[3];
+__device__ inline void split_pos(const double x[3], float (&h)[3], float (&l)[3]) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         const float xh = (float)x[a];
@@ -501,31 +515,36 @@ __device__ inline void store_pos(Work& w, int64_t q, const double x[3], double r
         h[a] = m * (1.0f / 1024.0f);
         l[a] = (xh - h[a]) + xl;
     }
+}
+__device__ inline void store_pos(Work& w, int64_t q, const double x[3], double rk, int tsrc) {
+    w.pos64[q] = dbl4_make(x[0], x[1], x[2], rk);
+    float h[3], l[3];
+    split_pos(x, h, l);
     w.rec[2 * q] = make_float4(h[0], h[1], h[2], __int_as_float(tsrc));
     w.rec[2 * q + 1] = make_float4(l[0], l[1], l[2], (float)rk);
     w.hi[q] = make_float4(h[0], h[1], h[2], __int_as_float(tsrc));
 }
 
-__global__ void k_fill_real(Work w, const int32_t* __restrict__ types, const double* __restrict__ rk_tab) {
-    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= w.Nr) return;
-    const int i = w.sorted_src[p];
-    int t = types[i];
-    if (t < 0 || t >= w.T) t = 0;
-    w.perm[p] = i;
-    w.sid[p] = w.sid_in[i];
-    w.cell_sorted[p] = w.cell_of[i];
-    w.slot_of[i] = (int)p;  // slot_of becomes the inverse permutation from here on
-    const double x[3] = {w.xw[3 * i], w.xw[3 * i + 1], w.xw[3 * i + 2]};
-    store_pos(w, p, x, rk_tab[t], t | ((int)p << 4));
-}
-
-// An image's FP64 position is its source's plus the lattice translation; its
-// split is the source's split plus the translation's (grid parts add exactly),
-// moved back to the nearest grid point (|lo| <= 2^-11) by whole grid steps.
-__global__ void k_fill_ghost(Work w, const int32_t* __restrict__ types, const double* __restrict__ rk_tab) {
-    int q = blockIdx.x * blockDim.x + threadIdx.x;
-    int ng = w.start_ghost[w.ncells];
+// Sorted positions: threads [0, Nr) fill the real atoms' slots, the next ones the
+// images'.  An image's FP64 position is its source's plus the lattice
+// translation; its split is the source's split plus the translation's (grid
+// parts add exactly), moved back to the nearest grid point (|lo| <= 2^-11) by
+// whole grid steps.
+__global__ void k_fill(Work w, const int32_t* __restrict__ types, const double* __restrict__ rk_tab) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < w.Nr) {
+        const int i = w.sorted_src[p];
+        int t = types[i];
+        if (t < 0 || t >= w.T) t = 0;
+        w.perm[p] = i;
+        w.sid[p] = w.sid_in[i];
+        w.cell_sorted[p] = w.cell_of[i];
+        const double x[3] = {w.xw[3 * i], w.xw[3 * i + 1], w.xw[3 * i + 2]};
+        store_pos(w, p, x, rk_tab[t], t | ((int)p << 4));
+        return;
+    }
+    const int64_t q = p - w.Nr;
+    const int ng = w.start_ghost[w.ncells];
     if (q >= ng) return;
     const int g = w.gsorted[q];
     const int i = w.ghost_src[g];
@@ -534,14 +553,15 @@ __global__ void k_fill_ghost(Work w, const int32_t* __restrict__ types, const do
     const StructGeo& G = w.geo[w.ghost_sid[g]];
     int t = types[i];
     if (t < 0 || t >= w.T) t = 0;
-    const int ps = w.slot_of[i];  // the source's sorted slot (written by k_fill_real)
+    const int ps = w.slot_of[i];  // the source's sorted slot (inverse permutation of the sort)
     const double rk = rk_tab[t];
-    double x[3] = {w.xw[3 * i], w.xw[3 * i + 1], w.xw[3 * i + 2]};
+    const double xs[3] = {w.xw[3 * i], w.xw[3 * i + 1], w.xw[3 * i + 2]};
+    double x[3] = {xs[0], xs[1], xs[2]};
     add_lattice(x, G, n0, n1, n2);
     w.pos64[w.Nr + q] = dbl4_make(x[0], x[1], x[2], rk);
-    const float4 hs = w.rec[2 * ps], ls = w.rec[2 * ps + 1];
+    float sh[3], sl[3];  // the source's split, as its own slot holds it
+    split_pos(xs, sh, sl);
     const float f0 = (float)n0, f1 = (float)n1, f2 = (float)n2;
-    const float sh[3] = {hs.x, hs.y, hs.z}, sl[3] = {ls.x, ls.y, ls.z};
     float h[3], l[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -553,7 +573,7 @@ __global__ void k_fill_ghost(Work w, const int32_t* __restrict__ types, const do
     }
     const int tsrc = t | (ps << 4);
     w.rec[2 * (w.Nr + q)] = make_float4(h[0], h[1], h[2], __int_as_float(tsrc));
-    w.rec[2 * (w.Nr + q) + 1] = make_float4(l[0], l[1], l[2], ls.w);
+    w.rec[2 * (w.Nr + q) + 1] = make_float4(l[0], l[1], l[2], (float)rk);
     w.hi[w.Nr + q] = make_float4(h[0], h[1], h[2], __int_as_float(tsrc));
 }
 
@@ -883,11 +903,11 @@ __global__ void __launch_bounds__(128) k_build_clist(Work w) {
 
 inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
-cudaError_t scan(const int* cnt, int* start, int* bsum, int64_t n, const int* gate, cudaStream_t st) {
+cudaError_t scan2(const ScanPair& sp, int* bsum, int64_t n, const int* gate, cudaStream_t st) {
     const int nb = (int)nblk(n, kScanBlock);
-    k_scan_blocks<<<nb, kScanBlock, 0, st>>>(cnt, start, bsum, n, gate);
-    k_scan_sums<<<1, kScanBlock, 0, st>>>(bsum, nb, start, n, gate);
-    k_scan_add<<<nb, kScanBlock, 0, st>>>(start, bsum, n, gate);
+    k_scan_blocks<<<dim3(nb, 2), kScanBlock, 0, st>>>(sp, bsum, nb, n, gate);
+    k_scan_sums<<<2, kScanBlock, 0, st>>>(sp, bsum, nb, n, gate);
+    k_scan_add<<<dim3(nb, 2), kScanBlock, 0, st>>>(sp, bsum, nb, n, gate);
     return cudaGetLastError();
 }
 
@@ -906,15 +926,12 @@ cudaError_t launch_build_impl(const Work& w, const double* pos, const int32_t* t
     k_reset<<<nblk(nreset, TB), TB, 0, st>>>(w);
     k_wrap<<<nblk(w.Nr, TB), TB, 0, st>>>(w, pos, types);
     k_images<<<nblk(w.Nr, TB), TB, 0, st>>>(w);
-    cudaError_t e = scan(w.cnt_real, w.start_real, bsum, w.ncells, w.gate, st);
+    const ScanPair sp{{w.cnt_real, w.cnt_ghost}, {w.start_real, w.start_ghost}};
+    const cudaError_t e = scan2(sp, bsum, w.ncells, w.gate, st);
     if (e != cudaSuccess) return e;
-    e = scan(w.cnt_ghost, w.start_ghost, bsum, w.ncells, w.gate, st);
-    if (e != cudaSuccess) return e;
-    k_scatter_real<<<nblk(w.Nr, TB), TB, 0, st>>>(w);
-    if (w.ghost_cap > 0) k_scatter_ghost<<<nblk(w.ghost_cap, TB), TB, 0, st>>>(w);
+    k_scatter<<<nblk(w.Nr + w.ghost_cap, TB), TB, 0, st>>>(w);
     k_sort_cells<<<nblk(w.ncells, TB), TB, 0, st>>>(w);
-    k_fill_real<<<nblk(w.Nr, TB), TB, 0, st>>>(w, types, rk_tab);
-    if (w.ghost_cap > 0) k_fill_ghost<<<nblk(w.ghost_cap, TB), TB, 0, st>>>(w, types, rk_tab);
+    k_fill<<<nblk(w.Nr + w.ghost_cap, TB), TB, 0, st>>>(w, types, rk_tab);
     {
         // persistent warps: w.build_per_sm blocks per SM, work handed out per 32 atoms
         // (per-atom lists) and per cluster (cluster lists)
@@ -932,7 +949,7 @@ cudaError_t launch_build_impl(const Work& w, const double* pos, const int32_t* t
     return cudaGetLastError();
 }
 
-int64_t scan_scratch_ints(int64_t ncells) { return nblk(ncells, kScanBlock) + 1; }
+int64_t scan_scratch_ints(int64_t ncells) { return 2 * nblk(ncells, kScanBlock) + 2; }
 
 cudaError_t launch_check(const Work& w, const double* pos, cudaStream_t st) {
     if (w.Nr == 0) return cudaGetLastError();

@@ -302,6 +302,6 @@ cudaError_t launch_heat(int64_t n, const double* w_atom, const double* vel, doub
 constexpr int kForwardLaunches = 5;  // kernels per forward pass (B > 0, N > 0): CN, dispersion, chain, 2 sums
                                      // (one more with the three-body term; in cluster mode one more,
                                      // the fixed-point finish, and a second for image rows of v, dv)
-constexpr int kBuildLaunches = 15;   // kernels per neighbour build (N > 0): reset, wrap, images, 2 x 3 scan,
-                                     // 2 scatter, sort, 2 fill, lists (per-atom or cluster lists)
+constexpr int kBuildLaunches = 10;   // kernels per neighbour build (N > 0): reset, wrap, images, 3 scan (both
+                                     // count arrays), scatter, sort, fill, lists (per-atom or cluster lists)
 }  // namespace d3gb

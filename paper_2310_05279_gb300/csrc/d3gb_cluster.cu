@@ -322,9 +322,11 @@ __global__ void __launch_bounds__(128, 3) k_disp_cl(Work w, Consts c, const floa
     }
     if (P.bad) atomicOr(w.status, ST_SUM_RANGE);
     // the cluster's virial, -sum_pairs fc d (x) d (the partials are of nfc d (x) d), and
-    // without SITE its energy, in FP64 on its first atom (the per-structure sums use
-    // them); zero on the others
-    double V[7];
+    // without SITE its energy: compensated float pairs summed over the warp in a fixed
+    // order, then lane m converts value m to FP64 (one conversion for all seven: the
+    // FP64 pipe takes a whole warp instruction however few lanes are active) and
+    // writes it on the cluster's first atom; zero on the others
+    float hm = 0.f, lm = 0.f;
 #pragma unroll
     for (int m = 0; m < 7; ++m) {
         if (m == 6 && SITE) break;
@@ -334,13 +336,19 @@ __global__ void __launch_bounds__(128, 3) k_disp_cl(Work w, Consts c, const floa
             h += __shfl_xor_sync(0xffffffffu, h, o);
             l += __shfl_xor_sync(0xffffffffu, l, o);
         }
-        V[m] = (double)h + (double)l;
+        if (lane == m) {
+            hm = h;
+            lm = l;
+        }
     }
-    if (js == 0 && ilive) {
+    const double Vm = (double)hm + (double)lm;
+    if (lane < 6) w.wv[6 * p0 + lane] = Vm;
+    if (!SITE && lane == 6) w.eat[p0] = Vm;
+    if (js == 0 && ilive && il > 0) {
         double* wv = w.wv + 6 * p;
 #pragma unroll
-        for (int m = 0; m < 6; ++m) wv[m] = il == 0 ? V[m] : 0.0;
-        if (!SITE) w.eat[p] = il == 0 ? V[6] : 0.0;
+        for (int m = 0; m < 6; ++m) wv[m] = 0.0;
+        if (!SITE) w.eat[p] = 0.0;
     }
 }
 

@@ -432,6 +432,8 @@ d3_status plan_alloc(d3_handle* h, Plan& P) {
     A(w.ghost_count, int, 1);
     A(w.sorted_src, int, Nr);
     A(w.gsorted, int, Ng);
+    A(w.usrc, int, Nr + Ng);
+    A(w.ukey, long long, Nr + Ng);
     A(w.pos64, dbl4, Nt);
     A(w.rec, float4, 2 * Nt);
     A(w.hi, float4, Nt);

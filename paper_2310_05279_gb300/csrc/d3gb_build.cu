@@ -8,7 +8,7 @@
 //   * explicit image atoms ("ghosts") for every periodic image that falls in
 //     that margin, so the pair kernels never apply lattice translations,
 //   * a counting sort of real atoms and of image atoms by cell (serpentine
-//     cell numbering; each cell is re-sorted by a deterministic key),
+//     cell numbering), each cell then ordered by a unique key (rank sort),
 //   * FP64 and split-FP32 (hi + lo) positions of every atom in sorted order,
 //   * per-atom neighbour lists within the two list radii, or (cluster mode)
 //     per-atom lists within the CN radius and, for the dispersion pass,
@@ -312,32 +312,12 @@ __global__ void k_scan_add(ScanPair sp, const int* __restrict__ bsum, int nb, in
     if (i < n) sp.start[a][i] += bsum[a * nb + blockIdx.x];
 }
 
-// ---- scatter into cell order: threads [0, Nr) the real atoms, then the images
-__global__ void k_scatter(Work w) {
-    if (skip_build(w)) return;
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < w.Nr) {
-        w.sorted_src[w.start_real[w.cell_of[i]] + w.slot_of[i]] = (int)i;
-        return;
-    }
-    const int64_t g = i - w.Nr;
-    const int ng = min(*w.ghost_count, w.ghost_cap);
-    if (g >= ng) return;
-    w.gsorted[w.start_ghost[w.ghost_cell[g]] + w.ghost_slot[g]] = (int)g;
-}
-
+// ---- cell order
 // Deterministic order inside each cell: real atoms by their position along the
 // cell's row in the direction the serpentine numbering runs (ties by input
 // index), so that runs of consecutive sorted atoms, the clusters of the
-// dispersion pass, are compact; images by (source, translation).  A block takes 256 consecutive cells, whose atoms
-// form one contiguous slice of sorted slots: the slice is staged in shared
-// memory, each thread insertion-sorts its own cell there, and the slice is
-// written back.  A slice larger than the stage is sorted in place in global
-// memory instead.  The sort also writes the inverse permutation of the real
-// atoms (slot_of[i] = sorted slot of input atom i; until then slot_of holds the
-// atoms' places in their cells, which the scatter has used).
-constexpr int kSortStage = 2048;
-
+// dispersion pass, are compact; images by (source, translation).  Both keys are
+// unique 64-bit integers.
 __device__ __forceinline__ long long image_key(const Work& w, int g) {
     return ((long long)w.ghost_src[g] << 24) | (long long)w.ghost_shift[g];
 }
@@ -350,108 +330,50 @@ __device__ __forceinline__ long long real_key(const Work& w, int i) {
     return (long long)(((unsigned long long)float_order(w.skey[i]) << 32) | (unsigned)i);
 }
 
-__global__ void __launch_bounds__(256) k_sort_cells(Work w) {
-    if (skip_build(w)) return;  // uniform over the grid
-    __shared__ int sr[kSortStage];
-    __shared__ int sg[kSortStage];
-    __shared__ long long sk[kSortStage];
-    const int64_t c0 = (int64_t)blockIdx.x * blockDim.x;
-    const int64_t c1 = c0 + blockDim.x < w.ncells ? c0 + blockDim.x : w.ncells;
-    const int64_t c = c0 + threadIdx.x;
-    const bool live = c < w.ncells;
-    {
-        const int lo = w.start_real[c0], hi = w.start_real[c1];
-        const bool fits = hi - lo <= kSortStage;
-        if (fits)
-            for (int k = lo + threadIdx.x; k < hi; k += blockDim.x) {
-                const int i = w.sorted_src[k];
-                sr[k - lo] = i;
-                sk[k - lo] = real_key(w, i);
-            }
-        __syncthreads();
-        if (live) {
-            const int b = w.start_real[c], e = w.start_real[c + 1];
-            if (fits) {
-                for (int k = b + 1 - lo; k < e - lo; ++k) {
-                    const int i = sr[k];
-                    const long long key = sk[k];
-                    int m = k - 1;
-                    while (m >= b - lo && sk[m] > key) {
-                        sk[m + 1] = sk[m];
-                        sr[m + 1] = sr[m];
-                        --m;
-                    }
-                    sk[m + 1] = key;
-                    sr[m + 1] = i;
-                }
-            } else {
-                for (int k = b + 1; k < e; ++k) {
-                    const int i = w.sorted_src[k];
-                    const long long key = real_key(w, i);
-                    int m = k - 1;
-                    while (m >= b) {
-                        const int h = w.sorted_src[m];
-                        if (real_key(w, h) <= key) break;
-                        w.sorted_src[m + 1] = h;
-                        --m;
-                    }
-                    w.sorted_src[m + 1] = i;
-                }
-                for (int k = b; k < e; ++k) w.slot_of[w.sorted_src[k]] = k;
-            }
-        }
-        __syncthreads();
-        if (fits)
-            for (int k = lo + threadIdx.x; k < hi; k += blockDim.x) {
-                const int i = sr[k - lo];
-                w.sorted_src[k] = i;
-                w.slot_of[i] = k;
-            }
-        __syncthreads();  // sk is reused for the images below
+// Scatter into cell order by the slots the binning reserved (an arbitrary order
+// inside each cell), with each slot's key: threads [0, Nr) the real atoms, then
+// the images (slots Nr + ... of usrc and ukey).
+__global__ void k_scatter(Work w) {
+    if (skip_build(w)) return;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < w.Nr) {
+        const int k = w.start_real[w.cell_of[i]] + w.slot_of[i];
+        w.usrc[k] = (int)i;
+        w.ukey[k] = real_key(w, (int)i);
+        return;
     }
-    {
-        const int lo = w.start_ghost[c0], hi = w.start_ghost[c1];
-        const bool fits = hi - lo <= kSortStage;
-        if (fits)
-            for (int k = lo + threadIdx.x; k < hi; k += blockDim.x) {
-                const int g = w.gsorted[k];
-                sg[k - lo] = g;
-                sk[k - lo] = image_key(w, g);
-            }
-        __syncthreads();
-        if (live) {
-            const int b = w.start_ghost[c], e = w.start_ghost[c + 1];
-            if (fits) {
-                for (int k = b + 1 - lo; k < e - lo; ++k) {
-                    const int g = sg[k];
-                    const long long key = sk[k];
-                    int m = k - 1;
-                    while (m >= b - lo && sk[m] > key) {
-                        sk[m + 1] = sk[m];
-                        sg[m + 1] = sg[m];
-                        --m;
-                    }
-                    sk[m + 1] = key;
-                    sg[m + 1] = g;
-                }
-            } else {
-                for (int k = b + 1; k < e; ++k) {
-                    const int g = w.gsorted[k];
-                    const long long key = image_key(w, g);
-                    int m = k - 1;
-                    while (m >= b) {
-                        const int h = w.gsorted[m];
-                        if (image_key(w, h) <= key) break;
-                        w.gsorted[m + 1] = h;
-                        --m;
-                    }
-                    w.gsorted[m + 1] = g;
-                }
-            }
-        }
-        __syncthreads();
-        if (fits)
-            for (int k = lo + threadIdx.x; k < hi; k += blockDim.x) w.gsorted[k] = sg[k - lo];
+    const int64_t g = i - w.Nr;
+    const int ng = min(*w.ghost_count, w.ghost_cap);
+    if (g >= ng) return;
+    const int64_t k = w.Nr + w.start_ghost[w.ghost_cell[g]] + w.ghost_slot[g];
+    w.usrc[k] = (int)g;
+    w.ukey[k] = image_key(w, (int)g);
+}
+
+// Each slot's final place in its cell is the number of smaller keys in the cell
+// (one thread per slot; the threads of a cell read the same keys).  Writes the
+// sorted order and, for real atoms, its inverse (slot_of[i] = sorted slot of
+// input atom i; until here slot_of held the atoms' places in their cells).
+__global__ void __launch_bounds__(256) k_rank(Work w) {
+    if (skip_build(w)) return;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool real = t < w.Nr;
+    const int ng = min(*w.ghost_count, w.ghost_cap);
+    if (!real && t - w.Nr >= ng) return;
+    const int u = w.usrc[t];
+    const int c = real ? w.cell_of[u] : w.ghost_cell[u];
+    const int* start = real ? w.start_real : w.start_ghost;
+    const int64_t off = real ? 0 : w.Nr;
+    const int b = start[c], e = start[c + 1];
+    const long long mine = w.ukey[t];
+    const long long* key = w.ukey + off;
+    int rank = 0;
+    for (int m = b; m < e; ++m) rank += key[m] < mine ? 1 : 0;
+    if (real) {
+        w.sorted_src[b + rank] = u;
+        w.slot_of[u] = b + rank;
+    } else {
+        w.gsorted[b + rank] = u;
     }
 }
 
@@ -930,7 +852,7 @@ cudaError_t launch_build_impl(const Work& w, const double* pos, const int32_t* t
     const cudaError_t e = scan2(sp, bsum, w.ncells, w.gate, st);
     if (e != cudaSuccess) return e;
     k_scatter<<<nblk(w.Nr + w.ghost_cap, TB), TB, 0, st>>>(w);
-    k_sort_cells<<<nblk(w.ncells, TB), TB, 0, st>>>(w);
+    k_rank<<<nblk(w.Nr + w.ghost_cap, TB), TB, 0, st>>>(w);
     k_fill<<<nblk(w.Nr + w.ghost_cap, TB), TB, 0, st>>>(w, types, rk_tab);
     {
         // persistent warps: w.build_per_sm blocks per SM, work handed out per 32 atoms

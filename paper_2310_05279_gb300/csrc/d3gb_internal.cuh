@@ -130,6 +130,8 @@ struct Work {
     int* ghost_count;        // [1]
     int* sorted_src;         // [Nr] sorted -> input index
     int* gsorted;            // [ghost_cap] sorted image slot -> raw image record
+    int* usrc;               // [Nr + ghost_cap] cell order before the in-cell sort: input index / image record
+    long long* ukey;         // [Nr + ghost_cap] the in-cell sort key of each such slot
     // per atom, sorted
     dbl4* pos64;             // [Nr + ghost_cap]
     float4* rec;             // [2 * (Nr + ghost_cap)]: hi at 2q, lo at 2q + 1
@@ -303,5 +305,6 @@ constexpr int kForwardLaunches = 5;  // kernels per forward pass (B > 0, N > 0):
                                      // (one more with the three-body term; in cluster mode one more,
                                      // the fixed-point finish, and a second for image rows of v, dv)
 constexpr int kBuildLaunches = 10;   // kernels per neighbour build (N > 0): reset, wrap, images, 3 scan (both
-                                     // count arrays), scatter, sort, fill, lists (per-atom or cluster lists)
+                                     // count arrays), scatter, rank (in-cell sort), fill, lists (per-atom or
+                                     // cluster lists)
 }  // namespace d3gb

@@ -193,6 +193,25 @@ struct ClusterPass {
                    acc + 8 * (int64_t)(tsq >> 4) + (il < 4 ? 2 * b0 + b1 : 4), x);
     }
 
+    // j side of two steps at once (without SITE): the first two levels of each
+    // reduce-scatter leave partial sums of one component per lane in each half of
+    // the 8 lanes of j; one exchange between the halves then completes step A's
+    // component on lanes il < 4 and step B's on lanes il >= 4 (the same additions as
+    // flush_j), so every lane adds one value
+    __device__ __forceinline__ float part_j(float ntx, float nty, float ntz, float dnj) const {
+        const float k0v = (b0 ? ntz : ntx) + __shfl_xor_sync(0xffffffffu, b0 ? ntx : ntz, 1);
+        const float k1v = (b0 ? dnj : nty) + __shfl_xor_sync(0xffffffffu, b0 ? nty : dnj, 1);
+        return (b1 ? k1v : k0v) + __shfl_xor_sync(0xffffffffu, b1 ? k0v : k1v, 2);
+    }
+    __device__ __forceinline__ void flush_j2(int tsa, unsigned uma, float pa, int tsb, unsigned umb, float pb) {
+        const bool hi = il >= 4;
+        const float mv = (hi ? pb : pa) + __shfl_xor_sync(0xffffffffu, hi ? pa : pb, 4);
+        const unsigned um = hi ? umb : uma;
+        const int tsq = hi ? tsb : tsa;
+        const unsigned long long x = fix40(mv, bad);
+        red_add_if((um >> fshift) & 0xffu, acc + 8 * (int64_t)(tsq >> 4) + 2 * b0 + b1, x);
+    }
+
     __device__ __forceinline__ void step2(const JData<R>& A, const JData<R>& B) {
         float ax, ay, az, ar2, bx, by, bz, br2;
         bool ause, anear, buse, bnear;
@@ -208,8 +227,13 @@ struct ClusterPass {
         float atx, aty, atz, adn, ae, btx, bty, btz, bdn, be;
         pair(A, ax, ay, az, ar2, ause, atx, aty, atz, adn, ae);
         pair(B, bx, by, bz, br2, buse, btx, bty, btz, bdn, be);
-        flush_j(__float_as_int(A.h.w), uma, atx, aty, atz, adn, ae);
-        flush_j(__float_as_int(B.h.w), umb, btx, bty, btz, bdn, be);
+        if constexpr (SITE) {
+            flush_j(__float_as_int(A.h.w), uma, atx, aty, atz, adn, ae);
+            flush_j(__float_as_int(B.h.w), umb, btx, bty, btz, bdn, be);
+        } else {
+            const float pa = part_j(atx, aty, atz, adn), pb = part_j(btx, bty, btz, bdn);
+            flush_j2(__float_as_int(A.h.w), uma, pa, __float_as_int(B.h.w), umb, pb);
+        }
     }
 };
 

@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(32 * kAtmWarps) k_atm(Work w, Consts c, const 
             int q = 0, tq = 0;
             T dx = 0, dy = 0, dz = 0, r2 = 0, rkq = 0;
             if (k < k1) {
-                q = __ldg(row + k);
+                q = __ldg(row + list_off(k));
                 S.dist(q, dx, dy, dz, r2, tq, rkq);
                 in = S.inside(q, r2, rc3, c.rc3_2);
             }

@@ -536,21 +536,20 @@ struct ListLane {
         capd = G.cap_disp;
         capc = G.cap_cn;
     }
-    // stage q; the 8th entry of a group writes the group as one sector (rows
-    // and capacities are multiples of 8 ints, so groups are 32-byte aligned)
+    // stage q; the 8th entry of a group writes the group as two 16-byte stores
+    // (capacities are multiples of 8, and groups of 4 entries are 16-byte aligned)
     __device__ __forceinline__ static void push(int* L, int cap, int& n, int* b, int q) {
         b[n & 7] = q;
         if ((n & 7) == 7 && n < cap) {
-            int4* dst = reinterpret_cast<int4*>(L + (n - 7));
-            dst[0] = *reinterpret_cast<const int4*>(b);
-            dst[1] = *reinterpret_cast<const int4*>(b + 4);
+            *reinterpret_cast<int4*>(L + list_off(n - 7)) = *reinterpret_cast<const int4*>(b);
+            *reinterpret_cast<int4*>(L + list_off(n - 3)) = *reinterpret_cast<const int4*>(b + 4);
         }
         ++n;
     }
     __device__ __forceinline__ static void drain(int* L, int cap, int n, const int* b) {
         const int base = n & ~7;
         for (int k = base; k < n; ++k)
-            if (k < cap) L[k] = b[k & 7];
+            if (k < cap) L[list_off(k)] = b[k & 7];
     }
     __device__ __forceinline__ void add(int q, float r2, float rd2, float rn2) {
         if (r2 < rd2 && q != (int)p) {
@@ -717,7 +716,8 @@ __global__ void __launch_bounds__(128) k_build_clist(Work w) {
                 const bool in = live && q != first + i && fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < rn2;
                 const unsigned mi = __ballot_sync(full, in);
                 const int kc = nc[i] + __popc(mi & ((1u << lane) - 1u));
-                if (in && kc < capc) w.nbr_cn[list_row(G.list_base_cn, (int64_t)first + i - G.atom_base, capc) + kc] = q;
+                if (in && kc < capc)
+                    w.nbr_cn[list_row(G.list_base_cn, (int64_t)first + i - G.atom_base, capc) + list_off(kc)] = q;
                 nc[i] += __popc(mi);
             }
             // move the rest (fewer than 32) to the front

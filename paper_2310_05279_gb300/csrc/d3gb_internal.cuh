@@ -207,15 +207,21 @@ struct Consts {
     float k3h, k3l;            // k3 as a float pair (k3h + k3l)
 };
 
-// ---- neighbour lists: one row of `cap` entries per atom (cap a multiple of 8),
-// rows of a structure contiguous; each thread appends to and reads its own row
-__host__ __device__ inline int64_t list_row(int64_t base, int64_t local, int cap) { return base + local * (int64_t)cap; }
-__host__ __device__ inline int list_off(int k) { return k; }
+// ---- neighbour lists: `cap` entries per atom (cap a multiple of 8).  The rows of
+// 32 consecutive atoms of a structure are interleaved in groups of 4 entries:
+// entry k of local atom a is at base + (a / 32) 32 cap + (k / 4) 128 + (a % 32) 4 + k % 4,
+// so when the threads of a warp (consecutive atoms) each read entries k..k+3 of
+// their own rows, the warp reads 512 contiguous bytes.  list_row gives the
+// address of entry 0 of an atom's row, list_off(k) the offset of entry k from it.
+__host__ __device__ inline int64_t list_row(int64_t base, int64_t local, int cap) {
+    return base + (local >> 5) * 32 * (int64_t)cap + (local & 31) * 4;
+}
+__host__ __device__ inline int list_off(int k) { return (k >> 2) * 128 + (k & 3); }
 __host__ __device__ inline int round_cap(double c) {
     int v = (int)c;
     return (v + 7) & ~7;
 }
-__host__ __device__ inline int64_t list_size(int64_t natoms, int cap) { return natoms * (int64_t)cap; }
+__host__ __device__ inline int64_t list_size(int64_t natoms, int cap) { return ((natoms + 31) >> 5) * 32 * (int64_t)cap; }
 
 // 256-bit read-only load (sm_100 and later)
 __device__ __forceinline__ void ld8(const float* p, float4& a, float4& b) {

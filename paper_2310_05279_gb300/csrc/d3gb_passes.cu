@@ -268,13 +268,13 @@ __global__ void __launch_bounds__(128) k_cn(Work w, Consts c, const float4* __re
             return chain_coef(z, r2, r2l, rch, rcl, k1);
         };
         for (int k = 0; k < cnt; k += 4) {
-            const int4 q4 = __ldg(reinterpret_cast<const int4*>(row + k));
+            const int4 q4 = __ldg(reinterpret_cast<const int4*>(row + list_off(k)));
             float4 g4;
             g4.x = term(q4.x);
             g4.y = k + 1 < cnt ? term(q4.y) : 0.0f;
             g4.z = k + 2 < cnt ? term(q4.z) : 0.0f;
             g4.w = k + 3 < cnt ? term(q4.w) : 0.0f;
-            *reinterpret_cast<float4*>(grow + k) = g4;
+            *reinterpret_cast<float4*>(grow + list_off(k)) = g4;
         }
         float Nh, Nl;  // n = nint + nh + nl as a float pair
         two_sum((float)nint, nh, Nh, Nl);
@@ -460,8 +460,8 @@ __global__ void __launch_bounds__(128) k_chain(Work w, Consts c, const float4* _
         if constexpr (MIXED) {
             const float* grow = w.gcn + (LV.p - w.nbr_cn);
             for (int k = k0; k < k1e; k += 4) {
-                const int4 q4 = __ldg(reinterpret_cast<const int4*>(LV.p + k));
-                const float4 g4 = __ldg(reinterpret_cast<const float4*>(grow + k));
+                const int4 q4 = __ldg(reinterpret_cast<const int4*>(LV.p + list_off(k)));
+                const float4 g4 = __ldg(reinterpret_cast<const float4*>(grow + list_off(k)));
                 entry(q4.x, g4.x);  // entries past the end of the list have g = 0
                 entry(q4.y, g4.y);
                 entry(q4.z, g4.z);

@@ -325,6 +325,7 @@ d3_status plan_geometry(d3_handle* h, Plan& P, int32_t B, const int64_t* offsets
             G.fscale[k] = (double)nck / span;
             const double cw = span * width / (double)nck;
             G.win[k] = (int)std::min<long long>(nck, (long long)std::ceil(rl / cw));
+            G.win_cn[k] = (int)std::min<long long>(nck, (long long)std::ceil(rln / cw));
             nc_total *= nck;
         }
         if (nc_total > ((int64_t)1 << 26)) return fail(h, D3_ERR_ARG, "too many cells for structure " + std::to_string(s));

@@ -645,9 +645,11 @@ __global__ void __launch_bounds__(128) k_build_lists(Work w) {
 //                                                (i, src, n) and (src, i, -n) are one instance
 // The same walk writes the per-atom CN lists of the cluster's atoms (every
 // atom within the CN list radius of each, both directions).
-// One warp per cluster walks the union of its atoms' cell windows.  The rows
-// of cells (real and image atoms of each row: two index ranges per row) are
-// flattened: 32 ranges at a time, their lengths scanned across the lanes, then
+// One warp per cluster walks the union of its atoms' cell windows.  A row of
+// cells whose real atoms all precede the cluster in sorted order holds no entry
+// of its half list, so for it only the (smaller) window of the CN radius is
+// walked.  The rows of cells (real and image atoms of each row: two index
+// ranges per row) are flattened: 32 ranges at a time, their lengths scanned across the lanes, then
 // 32 candidates at a time, each lane finding its range by a binary search over
 // the scanned offsets held in the lanes.  Candidates are appended in walk
 // order (ballot compaction), so every list is deterministic.  Candidates within
@@ -695,6 +697,13 @@ __global__ void __launch_bounds__(128) k_build_clist(Work w) {
         const int y1 = min(G.ncell[1] - 1, __reduce_max_sync(full, cy) + G.win[1]);
         const int z0 = max(0, __reduce_min_sync(full, cz) - G.win[2]);
         const int z1 = min(G.ncell[2] - 1, __reduce_max_sync(full, cz) + G.win[2]);
+        // the window of the CN list radius
+        const int xc0 = max(0, __reduce_min_sync(full, cx) - G.win_cn[0]);
+        const int xc1 = min(G.ncell[0] - 1, __reduce_max_sync(full, cx) + G.win_cn[0]);
+        const int yc0 = max(0, __reduce_min_sync(full, cy) - G.win_cn[1]);
+        const int yc1 = min(G.ncell[1] - 1, __reduce_max_sync(full, cy) + G.win_cn[1]);
+        const int zc0 = max(0, __reduce_min_sync(full, cz) - G.win_cn[2]);
+        const int zc1 = min(G.ncell[2] - 1, __reduce_max_sync(full, cz) + G.win_cn[2]);
         const int ny = y1 - y0 + 1, nranges = 2 * ny * (z1 - z0 + 1);
         int* row = w.nbr_cl + G.list_base_cl + (I - G.clu_base) * (int64_t)G.cap_cl;
         const int cap = G.cap_cl, capc = G.cap_cn;
@@ -748,6 +757,15 @@ __global__ void __launch_bounds__(128) k_build_clist(Work w) {
                 if ((r & 1) == 0) {
                     b = __ldg(&w.start_real[cf]);
                     len = __ldg(&w.start_real[cl + 1]) - b;
+                    if (b + len <= (int)p0) {  // the whole row precedes the cluster: CN candidates only
+                        if (y < yc0 || y > yc1 || z < zc0 || z > zc1) {
+                            len = 0;
+                        } else {
+                            row_cells(G, y, z, xc0, xc1, cf, cl);
+                            b = __ldg(&w.start_real[cf]);
+                            len = __ldg(&w.start_real[cl + 1]) - b;
+                        }
+                    }
                 } else {
                     b = (int)w.Nr + __ldg(&w.start_ghost[cf]);
                     len = (int)w.Nr + __ldg(&w.start_ghost[cl + 1]) - b;

@@ -61,6 +61,7 @@ struct StructGeo {
     float Hh[9], Hl[9];
     int ncell[3];
     int win[3];       // window half-width (cells) covering the list radii
+    int win_cn[3];    // window half-width (cells) covering the CN list radius
     int img[3];       // image range, 0 along open axes
     int pbc[3];
     int64_t cell_base;

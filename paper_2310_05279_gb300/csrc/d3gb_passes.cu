@@ -416,29 +416,8 @@ __global__ void __launch_bounds__(128) k_chain(Work w, Consts c, const float4* _
         const int k1e = min(cnt, k0 + kChunk);
         T sxx = 0, syy = 0, szz = 0, sxy = 0, sxz = 0, syz = 0;
         T tm[6] = {0, 0, 0, 0, 0, 0}, gv[3] = {0, 0, 0}, mm[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-        auto entry = [&](int q, T g) {
-            T dx, dy, dz, dnq;
-            int srcq;
-            if constexpr (MIXED) {
-                if (g == 0.0f) return;  // outside R_cn (an exact zero adds nothing either)
-                float D[3], e[3];
-                int tq;
-                S.dist_exact(q, D, e, tq);
-                srcq = tq >> 4;
-                dnq = dEdn[srcq];
-                dx = D[0]; dy = D[1]; dz = D[2];
-            } else {
-                T r2, rkq;
-                int tsq;
-                S.dist(q, dx, dy, dz, r2, tsq, rkq);
-                if (!S.inside(q, r2, rc2, c.rc_cn2)) return;
-                const T rinv = inv_sqrt(r2);
-                T f, dfdr;
-                cn_fun(rinv, S.rk() + rkq, (T)0, k1, f, &dfdr);
-                g = dfdr * rinv;
-                srcq = tsq >> 4;
-                dnq = dEdn[srcq];
-            }
+        // one pair's chain-rule terms: pair vector d, coefficient g = f'(r)/r, partner's dE/dn
+        auto add_pair = [&](T dx, T dy, T dz, T g, T dnq, int srcq) {
             const T coef = (dni + dnq) * g;
             fx += coef * dx; fy += coef * dy; fz += coef * dz;
             // per-atom geometric sum for the virial (scaled by dE/dn_i below)
@@ -458,17 +437,52 @@ __global__ void __launch_bounds__(128) k_chain(Work w, Consts c, const float4* _
             }
         };
         if constexpr (MIXED) {
+            // the stored coefficients (g = 0 outside R_cn and past the end of the list); the
+            // loads of a group of kGroup entries are issued before any of their arithmetic, an
+            // entry with g = 0 reading atom p's own record (d = 0: it adds nothing)
+            constexpr int kGroup = 8;
             const float* grow = w.gcn + (LV.p - w.nbr_cn);
-            for (int k = k0; k < k1e; k += 4) {
-                const int4 q4 = __ldg(reinterpret_cast<const int4*>(LV.p + list_off(k)));
-                const float4 g4 = __ldg(reinterpret_cast<const float4*>(grow + list_off(k)));
-                entry(q4.x, g4.x);  // entries past the end of the list have g = 0
-                entry(q4.y, g4.y);
-                entry(q4.z, g4.z);
-                entry(q4.w, g4.w);
+            for (int k = k0; k < k1e; k += kGroup) {
+                int q[kGroup];
+                float g[kGroup];
+#pragma unroll
+                for (int h = 0; h < kGroup; h += 4) {
+                    int4 q4 = make_int4(0, 0, 0, 0);
+                    float4 g4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (k + h < k1e) {
+                        q4 = __ldg(reinterpret_cast<const int4*>(LV.p + list_off(k + h)));
+                        g4 = __ldg(reinterpret_cast<const float4*>(grow + list_off(k + h)));
+                    }
+                    q[h] = q4.x; q[h + 1] = q4.y; q[h + 2] = q4.z; q[h + 3] = q4.w;
+                    g[h] = g4.x; g[h + 1] = g4.y; g[h + 2] = g4.z; g[h + 3] = g4.w;
+                }
+                float D[kGroup][3];
+                int src[kGroup];
+#pragma unroll
+                for (int e = 0; e < kGroup; ++e) {
+                    float er[3];
+                    int tq;
+                    S.dist_exact(g[e] != 0.0f ? q[e] : (int)p, D[e], er, tq);
+                    src[e] = tq >> 4;
+                }
+                float dn[kGroup];
+#pragma unroll
+                for (int e = 0; e < kGroup; ++e) dn[e] = dEdn[src[e]];
+#pragma unroll
+                for (int e = 0; e < kGroup; ++e) add_pair(D[e][0], D[e][1], D[e][2], g[e], dn[e], src[e]);
             }
         } else {
-            LV.for_each(k0, k1e, [&](int q) { entry(q, (T)0); });
+            LV.for_each(k0, k1e, [&](int q) {
+                T dx, dy, dz, r2, rkq;
+                int tsq;
+                S.dist(q, dx, dy, dz, r2, tsq, rkq);
+                if (!S.inside(q, r2, rc2, c.rc_cn2)) return;
+                const T rinv = inv_sqrt(r2);
+                T f, dfdr;
+                cn_fun(rinv, S.rk() + rkq, (T)0, k1, f, &dfdr);
+                const int srcq = tsq >> 4;
+                add_pair(dx, dy, dz, dfdr * rinv, dEdn[srcq], srcq);
+            });
         }
         Sxx += (double)sxx; Syy += (double)syy; Szz += (double)szz;
         Sxy += (double)sxy; Sxz += (double)sxz; Syz += (double)syz;

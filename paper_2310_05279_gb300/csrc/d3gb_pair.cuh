@@ -165,8 +165,9 @@ __device__ __forceinline__ bool cn_pair_precise(const Site<true>& S, int q, cons
     float uh, ue;
     two_sum(rc.z, -Sh, uh, ue);
     const float ul = ue + (rc.w - Sl);
-    const float rh = Sh * rsqrt_nr(Sh);
-    const float rl = (fmaf(-rh, rh, Sh) + Sl) * (0.5f / rh);
+    const float y = rsqrt_nr(Sh);  // 1/r to FP32 precision: enough for the correction term below
+    const float rh = Sh * y;
+    const float rl = (fmaf(-rh, rh, Sh) + Sl) * (0.5f * y);
     const float ph = rh * rc.x, pe = fmaf(rh, rc.x, -ph);
     float dh, de;
     two_sum(Sh, ph, dh, de);

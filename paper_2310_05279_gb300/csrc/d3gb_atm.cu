@@ -149,7 +149,9 @@ __global__ void __launch_bounds__(32 * kAtmWarps) k_atm(Work w, Consts c, const 
                     sW[wid][slot][a] = Wq[a];
                 }
                 sa[slot] = T4{dx, dy, dz, r2};
-                sb[slot] = T4{C6, dC6 / C6, sR[ti * c.T + (tq & 15)], (T)1 / r2};
+                // FP32: Newton-refined reciprocals instead of IEEE divisions
+                const T gC6 = MIXED ? dC6 * rcp_t(C6) : dC6 / C6;
+                sb[slot] = T4{C6, gC6, sR[ti * c.T + (tq & 15)], rcp_t(r2)};
                 sq[slot] = make_int2(q, tq);
             }
             n += __popc(m);

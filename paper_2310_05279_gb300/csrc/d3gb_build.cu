@@ -47,7 +47,7 @@ __device__ inline int cell_id(const StructGeo& G, const float f[3], float* fx = 
     }
     const int64_t id = cell_index(G, c[0], c[1], c[2]);
     if (fx) {
-        const int64_t row = (id - G.cell_base) / G.ncell[0];
+        const int row = (int)(id - G.cell_base) / G.ncell[0];  // fewer than 2^26 cells per structure
         *fx = (row & 1) ? -u0 : u0;
     }
     return (int)id;

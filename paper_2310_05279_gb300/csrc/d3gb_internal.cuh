@@ -86,12 +86,13 @@ __host__ __device__ inline int64_t cell_index(const StructGeo& G, int cx, int cy
     const int xx = (row & 1) ? G.ncell[0] - 1 - cx : cx;
     return G.cell_base + row * G.ncell[0] + xx;
 }
+// (a structure has fewer than 2^26 cells, so 32-bit divisions suffice)
 __host__ __device__ inline void cell_coords(const StructGeo& G, int64_t id, int& cx, int& cy, int& cz) {
-    const int64_t rel = id - G.cell_base;
-    const int64_t row = rel / G.ncell[0];
-    const int xx = (int)(rel - row * G.ncell[0]);
-    cz = (int)(row / G.ncell[1]);
-    const int yy = (int)(row - (int64_t)cz * G.ncell[1]);
+    const int rel = (int)(id - G.cell_base);
+    const int row = rel / G.ncell[0];
+    const int xx = rel - row * G.ncell[0];
+    cz = row / G.ncell[1];
+    const int yy = row - cz * G.ncell[1];
     cy = (cz & 1) ? G.ncell[1] - 1 - yy : yy;
     cx = (row & 1) ? G.ncell[0] - 1 - xx : xx;
 }

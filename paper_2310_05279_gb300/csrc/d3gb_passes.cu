@@ -44,11 +44,6 @@ template <> struct PassAcc<false> {
     __device__ double total() const { return h; }
 };
 
-// CN pass, mixed form: pairs with a = k1 (rc/r - 1) below kCnFarA take the FP32
-// path, the others the double-single one (at most kCnStash of them set aside per atom)
-constexpr float kCnFarA = -8.0f;
-constexpr int kCnStash = 48;
-
 // Eq. 4 counting function f(r) and, optionally, df/dr, in FP64; r from 1/r.
 // (The mixed form evaluates it in double-single, cn_ds below.)
 __device__ __forceinline__ void cn_fun(double rinv, double rc_eff, double, double k1, double& f, double* dfdr) {
@@ -257,7 +252,7 @@ __global__ void __launch_bounds__(128) k_cn(Work w, Consts c, const float4* __re
         int nint = 0;  // terms with f > 1/2 are summed as 1 - t/(1 + t): exact integer part plus a small complement
         const int* row = LV.p;
         float* grow = w.gcn + (row - w.nbr_cn);
-        auto precise = [&](int q) -> float {  // the pair's CN term in double-single; returns f'(r)/r (0 outside R_cn)
+        auto term = [&](int q) -> float {  // the pair's CN term; returns f'(r)/r (0 outside R_cn)
             float D[3], r2, ah, al, rch, rcl, r2l;
             int tq;
             if (!cn_pair_precise(S, q, rrow, k1, rc2, c.rc_cn2, D, r2, ah, al, rch, tq, &rcl, &r2l)) return 0.0f;
@@ -272,50 +267,15 @@ __global__ void __launch_bounds__(128) k_cn(Work w, Consts c, const float4* __re
             }
             return chain_coef(z, r2, r2l, rch, rcl, k1);
         };
-        // Pass 1 over the row: a pair with a = k1 (rc/r - 1) < kCnFarA (f < 3.4e-4) is
-        // evaluated in FP32 (its absolute error, below 4e-10 per pair, is far under the
-        // double-single path's budget for n); the others are set aside in shared memory
-        // and evaluated in double-single in pass 2, so that a warp runs each path with
-        // its lanes converged.  (Beyond kCnStash near pairs the rest are evaluated inline.)
-        __shared__ unsigned short stash[kCnStash][128];  // list positions below 2^16
-        int nn = 0;
-        float fs = 0.0f;  // sum of the FP32 terms
-        auto quick = [&](int q, int k) -> float {
-            float dx, dy, dz, r2, rkq;
-            int tq;
-            S.dist(q, dx, dy, dz, r2, tq, rkq);
-            if (!S.inside(q, r2, rc2, c.rc_cn2)) return 0.0f;
-            const float rc = rrow[tq & 15].x;
-            const float y = rsqrt_nr(r2);
-            const float a = k1 * fmaf(rc, y, -1.0f);
-            if (a >= kCnFarA) {
-                if (nn < kCnStash && k < 65536) {
-                    stash[nn][threadIdx.x] = (unsigned short)k;
-                    ++nn;
-                    return 0.0f;  // written in pass 2
-                }
-                return precise(q);
-            }
-            // the intrinsic's relative error (about 1.4e-6 at |a| = 16) is that of a itself
-            const float t = __expf(-a);        // > e^8
-            const float f = rcp_nr(1.0f + t);
-            fs += f;
-            return -k1 * rc * (t * f * f) * (y * y * y);  // f'(r)/r = -k1 rc f (1 - f) / r^3, 1 - f = t f
-        };
         for (int k = 0; k < cnt; k += 4) {
             const int4 q4 = __ldg(reinterpret_cast<const int4*>(row + list_off(k)));
             float4 g4;
-            g4.x = quick(q4.x, k);
-            g4.y = k + 1 < cnt ? quick(q4.y, k + 1) : 0.0f;
-            g4.z = k + 2 < cnt ? quick(q4.z, k + 2) : 0.0f;
-            g4.w = k + 3 < cnt ? quick(q4.w, k + 3) : 0.0f;
+            g4.x = term(q4.x);
+            g4.y = k + 1 < cnt ? term(q4.y) : 0.0f;
+            g4.z = k + 2 < cnt ? term(q4.z) : 0.0f;
+            g4.w = k + 3 < cnt ? term(q4.w) : 0.0f;
             *reinterpret_cast<float4*>(grow + list_off(k)) = g4;
         }
-        for (int m = 0; m < nn; ++m) {  // pass 2: the near pairs
-            const int k = stash[m][threadIdx.x];
-            grow[list_off(k)] = precise(__ldg(row + list_off(k)));
-        }
-        acc_add(nh, nl, fs);
         float Nh, Nl;  // n = nint + nh + nl as a float pair
         two_sum((float)nint, nh, Nh, Nl);
         Nl += nl;

@@ -32,6 +32,12 @@ __device__ __forceinline__ float rcp_nr(float x) {
     return fmaf(y, e, y);
 }
 
+// s + err == a + b exactly when |a| >= |b| (Dekker's Fast2Sum); s, err may alias a, b
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& err) {
+    const float t = a + b;
+    err = b - (t - a);
+    s = t;
+}
 // s + err == a + b exactly (Knuth's TwoSum)
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& err) {
     s = a + b;
@@ -138,14 +144,16 @@ __device__ __forceinline__ void load_vec(const float* __restrict__ p, float (&x)
 
 // Mixed form: pair vector D (FP32), r^2 and the Eq. 4 exponent a = k1 (rc/r - 1)
 // as a double-single pair (ah + al) from the exact pair vector D + e:
-//   r^2 = Sh + Sl (TwoProd/TwoSum), u = rc^2 - r^2, r = sqrt(r^2) with its
-//   correction term, den = r^2 + r rc, a = k1 u / den with one residual step.
-// Its error is a few units of 2^-48 relative, so exp(-a) is as accurate as
-// expf itself.  Returns false when the pair is outside R_cn.
+//   r^2 = Sh + Sl (TwoProd/TwoSum), r = sqrt(r^2) with its correction term,
+//   d = rc - r (TwoSum of the double-single rc and r), a = k1 d / r with one
+//   residual step.
+// Its absolute error is about 1e-11 over the range of pair distances (a CPU
+// emulation against long double), far below the rounding of expf itself.
+// Returns false when the pair is outside R_cn.
 __device__ __forceinline__ bool cn_pair_precise(const Site<true>& S, int q, const float4* rrow, float k1, float rc2,
                                                 double rc2d, float (&D)[3], float& r2, float& ah, float& al,
                                                 float& rch, int& tq, float* rcl_out = nullptr,
-                                                float* r2l_out = nullptr) {
+                                                float* r2l_out = nullptr, float* y_out = nullptr) {
     float e[3];
     S.dist_exact(q, D, e, tq);
     float P[3], pl[3];
@@ -158,28 +166,24 @@ __device__ __forceinline__ bool cn_pair_precise(const Site<true>& S, int q, cons
     two_sum(P[0], P[1], S1, s1);
     two_sum(S1, P[2], Sh, s2);
     float Sl = (s1 + s2) + (pl[0] + pl[1] + pl[2]) + 2.0f * (D[0] * e[0] + D[1] * e[1] + D[2] * e[2]);
-    two_sum(Sh, Sl, Sh, Sl);  // normalise
+    fast_two_sum(Sh, Sl, Sh, Sl);  // normalise (|Sl| <= |Sh|)
     r2 = Sh;
     if (!S.inside(q, r2, rc2, rc2d)) return false;
-    const float4 rc = rrow[tq & 15];  // rc hi, rc lo, rc^2 hi, rc^2 lo
-    float uh, ue;
-    two_sum(rc.z, -Sh, uh, ue);
-    const float ul = ue + (rc.w - Sl);
-    const float y = rsqrt_nr(Sh);  // 1/r to FP32 precision: enough for the correction term below
+    const float4 rc = rrow[tq & 15];  // rc hi, rc lo (, rc^2 hi, rc^2 lo)
+    const float y = rsqrt_nr(Sh);  // 1/r to FP32 precision: enough for the correction terms below
     const float rh = Sh * y;
     const float rl = (fmaf(-rh, rh, Sh) + Sl) * (0.5f * y);
-    const float ph = rh * rc.x, pe = fmaf(rh, rc.x, -ph);
     float dh, de;
-    two_sum(Sh, ph, dh, de);
-    const float dl = de + Sl + pe + rh * rc.y + rl * rc.x;
-    const float idh = rcp_nr(dh);
-    const float qh = uh * idh;
-    const float ql = (fmaf(-qh, dh, uh) + ul - qh * dl) * idh;
+    two_sum(rc.x, -rh, dh, de);
+    const float dl = de + (rc.y - rl);
+    const float qh = dh * y;  // q = d / r
+    const float ql = (fmaf(-qh, rh, dh) + dl - qh * rl) * y;
     ah = k1 * qh;
     al = fmaf(k1, qh, -ah) + k1 * ql;
     rch = rc.x;
     if (rcl_out) *rcl_out = rc.y;
     if (r2l_out) *r2l_out = Sl;
+    if (y_out) *y_out = y;  // rsqrt_nr(r2), for chain_coef
     return true;
 }
 
@@ -263,8 +267,9 @@ __device__ __forceinline__ void ds_mul(float ah, float al, float bh, float bl, f
 // Chain-rule coefficient f'(r)/r = -k1 rc f (1 - f) / r^3 of Eq. 4, formed in
 // double-single and rounded once: 1/r from r^2 = r2 + r2l with one residual
 // step, the exact rc = rch + rcl, f and 1 - f from cn_ds.
-__device__ __forceinline__ float chain_coef(const CnDS& z, float r2, float r2l, float rch, float rcl, float k1) {
-    const float y0 = rsqrt_nr(r2);
+// (y0 = rsqrt_nr(r2), when the caller has it already)
+__device__ __forceinline__ float chain_coef(const CnDS& z, float y0, float r2, float r2l, float rch, float rcl,
+                                           float k1) {
     const float y2 = y0 * y0, y2e = fmaf(y0, y0, -y2);
     const float ry = fmaf(-r2, y2, 1.0f) - fmaf(r2, y2e, r2l * y2);
     const float yh = y0, yl = 0.5f * y0 * ry;
@@ -275,6 +280,9 @@ __device__ __forceinline__ float chain_coef(const CnDS& z, float r2, float r2l, 
     ds_mul(rch, rcl, cfh, cfl, uh, ul);
     ds_mul(uh, ul, a3h, a3l, gh, gl);
     return -k1 * (gh + gl);
+}
+__device__ __forceinline__ float chain_coef(const CnDS& z, float r2, float r2l, float rch, float rcl, float k1) {
+    return chain_coef(z, rsqrt_nr(r2), r2, r2l, rch, rcl, k1);
 }
 
 }  // namespace

@@ -253,9 +253,9 @@ __global__ void __launch_bounds__(128) k_cn(Work w, Consts c, const float4* __re
         const int* row = LV.p;
         float* grow = w.gcn + (row - w.nbr_cn);
         auto term = [&](int q) -> float {  // the pair's CN term; returns f'(r)/r (0 outside R_cn)
-            float D[3], r2, ah, al, rch, rcl, r2l;
+            float D[3], r2, ah, al, rch, rcl, r2l, y;
             int tq;
-            if (!cn_pair_precise(S, q, rrow, k1, rc2, c.rc_cn2, D, r2, ah, al, rch, tq, &rcl, &r2l)) return 0.0f;
+            if (!cn_pair_precise(S, q, rrow, k1, rc2, c.rc_cn2, D, r2, ah, al, rch, tq, &rcl, &r2l, &y)) return 0.0f;
             const CnDS z = cn_ds(ah, al, exptab);
             if (z.th < 1.0f) {
                 ++nint;
@@ -265,7 +265,7 @@ __global__ void __launch_bounds__(128) k_cn(Work w, Consts c, const float4* __re
                 acc_add(nh, nl, z.fh);
                 nl += z.fl;
             }
-            return chain_coef(z, r2, r2l, rch, rcl, k1);
+            return chain_coef(z, y, r2, r2l, rch, rcl, k1);
         };
         for (int k = 0; k < cnt; k += 4) {
             const int4 q4 = __ldg(reinterpret_cast<const int4*>(row + list_off(k)));

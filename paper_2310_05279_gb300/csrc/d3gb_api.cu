@@ -131,6 +131,7 @@ struct d3_handle {
     float2* d_exptab = nullptr;  // 2^(j/64), j = 0..63, FP32 hi + lo
     double* d_rk = nullptr;
     int* d_status = nullptr;
+    int* h_status = nullptr;                 // pinned host word for the status read of the host-buffer path
     unsigned long long* d_nbuild = nullptr;  // builds executed on the device
     cudaStream_t last_stream = nullptr;
     std::string err;
@@ -1023,6 +1024,7 @@ void d3_destroy(d3_handle* h) {
     h->plan.mem.release();
     h->stage.release();
     h->tabmem.release();
+    if (h->h_status) cudaFreeHost(h->h_status);
     delete h;
 }
 
@@ -1144,6 +1146,8 @@ d3_status d3_compute(d3_handle* h, const double* pos, const int32_t* types, int6
     return forward_graph(h, 1, off, pos, types, cell, pbc, E, F, W, nullptr, nullptr, (cudaStream_t)stream, nullptr);
 }
 
+static d3_status status_of_word(d3_handle* h, int st);
+
 d3_status d3_compute_batch_host(d3_handle* h, int32_t B, const int64_t* offsets, const double* pos,
                                 const int32_t* types, const double* cells, const int32_t* pbc, double* E,
                                 double* F, double* W, void* stream) {
@@ -1173,12 +1177,22 @@ d3_status d3_compute_batch_host(d3_handle* h, int32_t B, const int64_t* offsets,
     s = forward_graph(h, B, offsets, h->s_pos, h->s_types, cells, pbc, h->s_E, h->s_F, h->s_W, nullptr, nullptr, st,
                       nullptr);
     if (s != D3_OK) return s;
+    if (!h->h_status) {
+        e = cudaHostAlloc(&h->h_status, sizeof(int), cudaHostAllocDefault);
+        if (e != cudaSuccess) {
+            h->h_status = nullptr;
+            return cuda_fail(h, e, "status word allocation");
+        }
+    }
     e = cudaMemcpyAsync(E, h->s_E, B * sizeof(double), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(F, h->s_F, 3 * N * sizeof(double), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(W, h->s_W, 9 * (size_t)B * sizeof(double), cudaMemcpyDeviceToHost, st);
+    // the status word travels with the outputs and is cleared on the same stream: one synchronisation
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->h_status, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_status, 0, sizeof(int), st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(h, e, "output copy");
-    return d3_sync_status(h);
+    return status_of_word(h, *h->h_status);
 }
 
 d3_status d3_backward(d3_handle* h, int32_t B, const int64_t* offsets, const double* pos, const int32_t* types,
@@ -1226,14 +1240,8 @@ d3_status d3_backward(d3_handle* h, int32_t B, const int64_t* offsets, const dou
     return D3_OK;
 }
 
-d3_status d3_sync_status(d3_handle* h) {
-    if (!h) return D3_ERR_ARG;
-    cudaError_t e = cudaStreamSynchronize(h->last_stream);
-    if (e != cudaSuccess) return cuda_fail(h, e, "synchronize");
-    int st = 0;
-    e = cudaMemcpy(&st, h->d_status, sizeof(int), cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess) e = cudaMemset(h->d_status, 0, sizeof(int));
-    if (e != cudaSuccess) return cuda_fail(h, e, "status read");
+// The status word's flags as a library status (and the error text).
+static d3_status status_of_word(d3_handle* h, int st) {
     if (st & ST_NONFINITE) return fail(h, D3_ERR_NONFINITE, "non-finite coordinate");
     if (st & ST_TYPE) return fail(h, D3_ERR_TYPE, "atom type out of range");
     if (st & ST_RANGE)
@@ -1247,6 +1255,17 @@ d3_status d3_sync_status(d3_handle* h) {
     }
     h->err.clear();
     return D3_OK;
+}
+
+d3_status d3_sync_status(d3_handle* h) {
+    if (!h) return D3_ERR_ARG;
+    cudaError_t e = cudaStreamSynchronize(h->last_stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "synchronize");
+    int st = 0;
+    e = cudaMemcpy(&st, h->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(h->d_status, 0, sizeof(int));
+    if (e != cudaSuccess) return cuda_fail(h, e, "status read");
+    return status_of_word(h, st);
 }
 
 const char* d3_last_error(const d3_handle* h) { return h ? h->err.c_str() : "NULL handle"; }

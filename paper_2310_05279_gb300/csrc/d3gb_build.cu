@@ -649,9 +649,10 @@ __global__ void __launch_bounds__(128) k_build_lists(Work w) {
 // cells whose real atoms all precede the cluster in sorted order holds no entry
 // of its half list, so for it only the (smaller) window of the CN radius is
 // walked.  The rows of cells (real and image atoms of each row: two index
-// ranges per row) are flattened: 32 ranges at a time, their lengths scanned across the lanes, then
-// 32 candidates at a time, each lane finding its range by a binary search over
-// the scanned offsets held in the lanes.  Candidates are appended in walk
+// ranges per row) are flattened: 32 ranges at a time, their lengths scanned
+// across the lanes and the non-empty ones compacted in shared memory, then 32
+// candidates at a time, each lane finding its range by counting the range
+// starts at or before its candidate (one OR-reduction of start bits, a popcount).  Candidates are appended in walk
 // order (ballot compaction), so every list is deterministic.  Candidates within
 // the CN list radius of the bounding box are first staged in shared memory, in
 // walk order, and tested against the cluster's atoms 32 at a time.
@@ -665,7 +666,10 @@ __global__ void __launch_bounds__(128) k_build_clist(Work w) {
     __shared__ float4 sh_i[4][kClusterAtoms];  // the cluster's atoms (hi positions) per warp
     __shared__ float4 sh_ch[4][64];            // staged CN candidates per warp: position, index
     __shared__ int sh_cq[4][64];
+    __shared__ int sh_rb[4][32], sh_re[4][32];  // the batch's non-empty ranges: first index (bit 31: images), start
     float4* hi8 = sh_i[threadIdx.x >> 5];
+    int* rb = sh_rb[threadIdx.x >> 5];
+    int* re = sh_re[threadIdx.x >> 5];
     float4* ch = sh_ch[threadIdx.x >> 5];
     int* cq = sh_cq[threadIdx.x >> 5];
     for (;;) {
@@ -779,17 +783,28 @@ __global__ void __launch_bounds__(128) k_build_clist(Work w) {
             }
             const int excl = incl - len;
             const int total = __shfl_sync(full, incl, 31);
+            // the non-empty ranges in order, in shared memory (their starts are distinct)
+            const unsigned ne = __ballot_sync(full, len > 0);
+            __syncwarp();
+            if (len > 0) {
+                const int k = __popc(ne & ((1u << lane) - 1u));
+                rb[k] = (int)((unsigned)b | ((unsigned)(r & 1) << 31));
+                re[k] = excl;
+            }
+            __syncwarp();
+            int c0 = 0;  // non-empty ranges that start before f0
             for (int f0 = 0; f0 < total; f0 += 32) {
                 const int f = f0 + lane;
-                // the range holding flat candidate f: the last lane k with excl_k <= f
-                int k = 0;
-#pragma unroll
-                for (int step = 16; step > 0; step >>= 1) {
-                    const int e = __shfl_sync(full, excl, k + step);
-                    if (e <= f) k += step;
-                }
-                const int q = __shfl_sync(full, b, k) + (f - __shfl_sync(full, excl, k));
-                const bool img = ((r0 + k) & 1) != 0;
+                // the range holding flat candidate f: the last non-empty range starting at or
+                // before f, counted from one bit per range start in [f0, f0 + 32)
+                const int d = excl - f0;
+                const unsigned M = __reduce_or_sync(full, (len > 0 && d >= 0 && d < 32) ? (1u << d) : 0u);
+                const int k = c0 + __popc(M & (0xffffffffu >> (31 - lane))) - 1;
+                c0 += __popc(M);
+                const int kr = f < total ? k : 0;
+                const int rbk = rb[kr];
+                const int q = (rbk & 0x7fffffff) + (f - re[kr]);
+                const bool img = rbk < 0;
                 bool take = false, cn_cand = false;
                 float4 hq = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (f < total) {

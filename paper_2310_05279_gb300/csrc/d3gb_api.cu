@@ -434,6 +434,9 @@ d3_status plan_alloc(d3_handle* h, Plan& P) {
     A(w.ghost_count, int, 1);
     A(w.sorted_src, int, Nr);
     A(w.gsorted, int, Ng);
+    A(w.ginv, int, Ng);
+    A(w.gfirst, int, Nr);
+    A(w.gcnt, int, Nr);
     A(w.usrc, int, Nr + Ng);
     A(w.ukey, long long, Nr + Ng);
     A(w.pos64, dbl4, Nt);
@@ -674,7 +677,7 @@ d3_status tune_shapes(d3_handle* h, Plan& P, const double* pos, const int32_t* t
             if (e == cudaSuccess) e = launch_forward(w, c, mixed, tb, E, F, W, nullptr, nullptr, nullptr, P.B, st,
                                                      ev.data() + 1);
             if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-            h->launches += kBuildLaunches + kForwardLaunches + c.atm + w.cl_mode * (1 + w.vd_images);
+            h->launches += kBuildLaunches + kForwardLaunches + c.atm + w.cl_mode;
             const int from[4] = {0, 1, 3, 5};
             for (int m = 0; m < 4 && e == cudaSuccess; ++m) {
                 float ms = 0.f;
@@ -816,7 +819,7 @@ d3_status forward(d3_handle* h, int32_t B, const int64_t* offsets, const double*
     cudaError_t e = launch_forward(P.w, c, mixed, tb, E, F, W, e_atom, cn, w_atom, B, st,
                                    ev.size() == kEvents ? ev.data() + 1 : nullptr);
     if (e != cudaSuccess) return cuda_fail(h, e, "forward launch");
-    h->launches += (P.Nr > 0 ? kForwardLaunches + c.atm + (mode == kClusterLists ? 1 + P.w.vd_images : 0) : 1);
+    h->launches += (P.Nr > 0 ? kForwardLaunches + c.atm + (mode == kClusterLists ? 1 : 0) : 1);
     if (ev.size() == kEvents) h->ev_pending.push_back(ev);
     else for (cudaEvent_t x : ev) h->ev_pool.push_back(x);
     return D3_OK;

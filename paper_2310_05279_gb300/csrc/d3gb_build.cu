@@ -210,6 +210,10 @@ __global__ void __launch_bounds__(256) k_images(Work w) {
         base = acc > 0 ? atomicAdd(w.ghost_count, acc) : 0;
     }
     __syncthreads();
+    if (live) {  // the atom's image records are consecutive from here
+        w.gfirst[i] = base + wsum[wid] + x - mine;
+        w.gcnt[i] = mine > 0 ? mine : 0;
+    }
     if (!live || mine <= 0) return;
     int slot = base + wsum[wid] + x - mine;
     auto cell_of_axis = [&](int k, int n) {
@@ -374,6 +378,7 @@ __global__ void __launch_bounds__(256) k_rank(Work w) {
         w.slot_of[u] = b + rank;
     } else {
         w.gsorted[b + rank] = u;
+        w.ginv[u] = b + rank;
     }
 }
 

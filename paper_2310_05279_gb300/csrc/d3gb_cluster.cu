@@ -64,19 +64,6 @@ __device__ __forceinline__ void red_add_if(bool p, unsigned long long* a, unsign
                  :: "l"(a), "l"(x), "r"((unsigned)p) : "memory");
 }
 
-// Rows of v and dv for the image atoms, copies of their source atom's rows (used
-// when images x types is small against the real atoms), so that the pass reads a
-// neighbour's data at the neighbour's own index.  rows = T * 2 * RP floats per atom.
-__global__ void __launch_bounds__(256) k_vd_images(Work w, int rows) {
-    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= w.start_ghost[w.ncells]) return;
-    const int64_t q = w.Nr + g;
-    const int src = rec_tsrc(w, q) >> 4;
-    const float4* from = reinterpret_cast<const float4*>(w.vd + (int64_t)src * rows);
-    float4* to = reinterpret_cast<float4*>(w.vd + q * rows);
-    for (int k = 0; k < rows / 4; ++k) to[k] = __ldg(from + k);
-}
-
 // Data of one list entry for the lane's step: the neighbour's split position and
 // its rows v^(t_i), dv^(t_i) (its own, or its source atom's); q = -1 past the end
 // of the list.
@@ -396,7 +383,7 @@ inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
 cudaError_t launch_disp_cl(const Work& w, const Consts& c, const void* pair_tab, bool site, cudaStream_t st) {
     if (w.Nr == 0) return cudaGetLastError();
-    if (w.vd_images) k_vd_images<<<nblk(w.ghost_cap, 256), 256, 0, st>>>(w, c.T * 2 * c.RP);
+    // (with vd_images the CN pass has written the image atoms' rows of v and dv)
     if (w.ncl > 0) {
         const int TB = w.blk_disp;  // 64 or 128 threads: 2 or 4 clusters per block
         const unsigned grid = nblk(w.ncl, TB / 32);

@@ -132,6 +132,9 @@ struct Work {
     int* ghost_count;        // [1]
     int* sorted_src;         // [Nr] sorted -> input index
     int* gsorted;            // [ghost_cap] sorted image slot -> raw image record
+    int* ginv;               // [ghost_cap] raw image record -> sorted image slot
+    int* gfirst;             // [Nr] input atom -> its first raw image record (its images are consecutive)
+    int* gcnt;               // [Nr] input atom -> its number of image records
     int* usrc;               // [Nr + ghost_cap] cell order before the in-cell sort: input index / image record
     long long* ukey;         // [Nr + ghost_cap] the in-cell sort key of each such slot
     // per atom, sorted
@@ -161,7 +164,8 @@ struct Work {
                              // (written by the CN pass, 0 outside R_cn; read by the chain pass)
     float* vd;               // [Nr (+ ghost_cap)][T][2][RP] per atom q and partner type t: v_q^(t) and
                              // dv_q^(t)_a = sum_b C6ref[t][tq][a][b] dW_qb
-    int vd_images;           // 1: image atoms have rows (copies of their source's), 0: they use their source's
+    int vd_images;           // 1: image atoms have rows (copies of their source's, written by the CN pass),
+                             // 0: the dispersion pass reads their source's
     float* skey;             // [Nr] within-cell sort key (position along the serpentine direction), input order
     unsigned long long* npairs;  // [1] unique pairs within R_pot of the last cluster-mode dispersion pass
     // list reuse (skin > 0): the build kernels run only while *gate != 0
@@ -311,7 +315,7 @@ cudaError_t launch_atm(const Work& w, const Consts& c, bool mixed, const void* r
 cudaError_t launch_heat(int64_t n, const double* w_atom, const double* vel, double* J, cudaStream_t st);
 constexpr int kForwardLaunches = 5;  // kernels per forward pass (B > 0, N > 0): CN, dispersion, chain, 2 sums
                                      // (one more with the three-body term; in cluster mode one more,
-                                     // the fixed-point finish, and a second for image rows of v, dv)
+                                     // the fixed-point finish)
 constexpr int kBuildLaunches = 10;   // kernels per neighbour build (N > 0): reset, wrap, images, 3 scan (both
                                      // count arrays), scatter, rank (in-cell sort), fill, lists (per-atom or
                                      // cluster lists)

@@ -281,6 +281,16 @@ __global__ void __launch_bounds__(128) k_cn(Work w, Consts c, const float4* __re
         Nl += nl;
         w.cn[p] = (double)Nh + (double)Nl;
         weights_atom_mixed<R>(w, c, cnref2, dcr, nref, (const float*)c6, p, S.tsrc() & 15, Nh, Nl);
+        if (w.vd_images) {  // copies of the atom's v/dv rows for its image atoms (read back from this thread's writes)
+            const int rows4 = c.T * 2 * c.RP / 4;
+            const int i = w.perm[p];
+            const int g0 = w.gfirst[i], ng = w.gcnt[i];
+            const float4* from = reinterpret_cast<const float4*>(w.vd) + p * rows4;
+            for (int k = 0; k < ng && g0 + k < w.ghost_cap; ++k) {
+                float4* to = reinterpret_cast<float4*>(w.vd) + (w.Nr + w.ginv[g0 + k]) * (int64_t)rows4;
+                for (int m = 0; m < rows4; ++m) to[m] = from[m];
+            }
+        }
     } else {
         const T rki = S.rk();
         LV.for_each(0, cnt, [&](int q) {

@@ -9,7 +9,9 @@
 //                     v_i^(t)_a = sum_b C6ref[t][t_i][a][b] W_ib, so that
 //                     C6_ij = sum_a W_ia v_j^(t_i)_a
 //   k_disp     Eq. 2  site energy, direct forces, virial and
-//                     dE/dn_i = sum_j (dE/dC6_ij)(dC6_ij/dn_i)
+//                     dE/dn_i = sum_j (dE/dC6_ij)(dC6_ij/dn_i) (FP64 form and per-atom
+//                     virial; the mixed form's dispersion pass runs over cluster half
+//                     lists, d3gb_cluster.cu)
 //   k_atm             optional three-body term (not part of the paper's model;
 //                     d3gb_atm.cu), between the dispersion and chain passes
 //   k_chain           forces and virial of the coordination-number dependence:
@@ -225,13 +227,14 @@ __device__ __forceinline__ void weights_atom_mixed(const Work& w, const Consts& 
 
 // ------------------------------------------------------------------ Eq. 4
 // The coordination numbers feed dC6/dn, which can be large, so the mixed form
-// keeps n_i accurate to a few 1e-8: the pair vector is exact (D + e), r^2 is
-// formed in double-single, the argument k1 (rc/r - 1) is evaluated as
-// k1 (rc^2 - r^2) / (r (rc + r)) so its error is relative to its own size,
-// and the sum over neighbours is compensated.  The mixed form also stores, per
-// list entry, the chain-rule coefficient f'(r)/r of the pair (0 outside R_cn),
-// which depends on the geometry only: the chain pass reads it instead of forming
-// the double-single Eq. 4 term a second time.
+// keeps n_i accurate to a few 1e-8: the pair vector is exact (D + e), r^2 and
+// r are formed in double-single, the argument k1 (rc/r - 1) is evaluated as
+// k1 (rc - r) / r from the double-single difference rc - r, and the sum over
+// neighbours is compensated.  The mixed form also stores, per list entry, the
+// chain-rule coefficient f'(r)/r of the pair (0 outside R_cn), which depends on
+// the geometry only: the chain pass reads it instead of forming the
+// double-single Eq. 4 term a second time; and, when image atoms have rows of
+// their own, it writes the copies of the atom's v/dv rows for its images.
 template <bool MIXED, int R>
 __global__ void __launch_bounds__(128) k_cn(Work w, Consts c, const float4* __restrict__ rcpair,
                                            const float2* __restrict__ exptab, const double* __restrict__ cnref,

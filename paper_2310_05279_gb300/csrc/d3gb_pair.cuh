@@ -82,6 +82,10 @@ template <> struct Site<true> {
     __device__ void dist_exact(int q, float (&D)[3], float (&e)[3], int& tq) const {
         float4 hq, lq;
         rec_load(*w, q, hq, lq);
+        dist_exact(hq, lq, D, e, tq);
+    }
+    // the same from the neighbour's record, already loaded
+    __device__ void dist_exact(const float4& hq, const float4& lq, float (&D)[3], float (&e)[3], int& tq) const {
         const float A[3] = {hq.x - h.x, hq.y - h.y, hq.z - h.z};
         const float Bv[3] = {lq.x - l.x, lq.y - l.y, lq.z - l.z};
 #pragma unroll
@@ -153,9 +157,11 @@ __device__ __forceinline__ void load_vec(const float* __restrict__ p, float (&x)
 __device__ __forceinline__ bool cn_pair_precise(const Site<true>& S, int q, const float4* rrow, float k1, float rc2,
                                                 double rc2d, float (&D)[3], float& r2, float& ah, float& al,
                                                 float& rch, int& tq, float* rcl_out = nullptr,
-                                                float* r2l_out = nullptr, float* y_out = nullptr) {
+                                                float* r2l_out = nullptr, float* y_out = nullptr,
+                                                const float4* rec_q = nullptr) {
     float e[3];
-    S.dist_exact(q, D, e, tq);
+    if (rec_q) S.dist_exact(rec_q[0], rec_q[1], D, e, tq);  // q's record, loaded by the caller
+    else S.dist_exact(q, D, e, tq);
     float P[3], pl[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {

@@ -255,10 +255,11 @@ __global__ void __launch_bounds__(128) k_cn(Work w, Consts c, const float4* __re
         int nint = 0;  // terms with f > 1/2 are summed as 1 - t/(1 + t): exact integer part plus a small complement
         const int* row = LV.p;
         float* grow = w.gcn + (row - w.nbr_cn);
-        auto term = [&](int q) -> float {  // the pair's CN term; returns f'(r)/r (0 outside R_cn)
+        auto term = [&](int q, const float4* rec_q) -> float {  // the pair's CN term; returns f'(r)/r (0 outside R_cn)
             float D[3], r2, ah, al, rch, rcl, r2l, y;
             int tq;
-            if (!cn_pair_precise(S, q, rrow, k1, rc2, c.rc_cn2, D, r2, ah, al, rch, tq, &rcl, &r2l, &y)) return 0.0f;
+            if (!cn_pair_precise(S, q, rrow, k1, rc2, c.rc_cn2, D, r2, ah, al, rch, tq, &rcl, &r2l, &y, rec_q))
+                return 0.0f;
             const CnDS z = cn_ds(ah, al, exptab);
             if (z.th < 1.0f) {
                 ++nint;
@@ -271,12 +272,19 @@ __global__ void __launch_bounds__(128) k_cn(Work w, Consts c, const float4* __re
             return chain_coef(z, y, r2, r2l, rch, rcl, k1);
         };
         for (int k = 0; k < cnt; k += 4) {
+            // the four entries' records are loaded before any of their arithmetic (entries past
+            // the end of the list read atom p's own record, unused)
             const int4 q4 = __ldg(reinterpret_cast<const int4*>(row + list_off(k)));
+            const int qq[4] = {q4.x, k + 1 < cnt ? q4.y : (int)p, k + 2 < cnt ? q4.z : (int)p,
+                               k + 3 < cnt ? q4.w : (int)p};
+            float4 rq[4][2];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) rec_load(w, qq[e], rq[e][0], rq[e][1]);
             float4 g4;
-            g4.x = term(q4.x);
-            g4.y = k + 1 < cnt ? term(q4.y) : 0.0f;
-            g4.z = k + 2 < cnt ? term(q4.z) : 0.0f;
-            g4.w = k + 3 < cnt ? term(q4.w) : 0.0f;
+            g4.x = term(qq[0], rq[0]);
+            g4.y = k + 1 < cnt ? term(qq[1], rq[1]) : 0.0f;
+            g4.z = k + 2 < cnt ? term(qq[2], rq[2]) : 0.0f;
+            g4.w = k + 3 < cnt ? term(qq[3], rq[3]) : 0.0f;
             *reinterpret_cast<float4*>(grow + list_off(k)) = g4;
         }
         float Nh, Nl;  // n = nint + nh + nl as a float pair
